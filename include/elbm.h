@@ -1,0 +1,217 @@
+/*
+ * elbm.h -- C ABI of the GB300 (sm_103a) implementation of the entropic lattice
+ * Boltzmann method for the full-tensor anisotropic advection-diffusion equation
+ * (arXiv 2605.01774).
+ *
+ * Lattice: D3Q27 tensor-product set, c_i in {-1,0,1}^3, i = 9(cx+1)+3(cy+1)+(cz+1),
+ * W_i = (2/3)^(3-m_i) (1/6)^(m_i), cs^2 = 1/3, dx = dt = 1 (Section 2.1).
+ *
+ * One time step (Section 2.7): pull-stream, phi = sum g, j = sum c (g - g_eq),
+ * split g - g_eq = P(j) + dh, relax the flux with S = (I/2 + D/cs2)^-1
+ * (Eq. method-s-from-d), damp the ghost dh with the ADE-corrected entropic
+ * amplitude lambda (Eqs. method-lambda, method-correction), shorten the whole
+ * increment by the positivity fallback alpha (Eq. method-alpha), write back.
+ *
+ * Layout and ownership
+ *   Node (x, y, z) has linear index n = x + Nx (y + Ny z); every per-node field
+ *   is a plane of N = Nx Ny Nz values, vector fields are [k][N] (component
+ *   planes).  The library owns the population buffers and all derived data; the
+ *   caller owns every pointer it passes and keeps it alive only for the call.
+ *   Arguments documented "host or device" may point to either; the library asks
+ *   the CUDA runtime which one it is.  Device pointers must belong to the
+ *   current device.
+ *
+ * Streams and errors
+ *   Work is ordered on the stream given to elbm_create (NULL = legacy default
+ *   stream).  Calls that return data to host memory synchronise that stream;
+ *   elbm_step only enqueues.  Every call returns an elbm_status; there are no
+ *   exceptions across the ABI.  elbm_last_error() gives a message for the last
+ *   failing call on a handle.  Kernel-side problems (non-finite populations,
+ *   a timed-out wait) are reported by the next synchronising call.
+ *
+ * Thread safety: a handle may be used by one host thread at a time.
+ */
+#ifndef ELBM_H
+#define ELBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ELBM_OK = 0,
+    ELBM_ERR_ARG = 1,          /* bad argument (null, size, dtype, sizes mismatch) */
+    ELBM_ERR_NOT_SPD = 2,      /* diffusion tensor not symmetric positive definite */
+    ELBM_ERR_MACH = 3,         /* velocity makes an equilibrium weight P_i(u) <= 0 */
+    ELBM_ERR_OOM = 4,          /* device allocation failed */
+    ELBM_ERR_CUDA = 5,         /* CUDA runtime error (message in elbm_last_error) */
+    ELBM_ERR_NONFINITE = 6,    /* non-finite population detected by a reduction */
+    ELBM_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up */
+    ELBM_ERR_STATE = 8,        /* call not valid in the handle's state (e.g. no init) */
+    ELBM_ERR_UNSUPPORTED = 9   /* combination not available in this precision */
+} elbm_status;
+
+/* Storage and arithmetic of the populations.
+ *   ELBM_F64          FP64 storage, FP64 arithmetic.
+ *   ELBM_F32          FP32 storage, FP32 arithmetic.
+ *   ELBM_F32_F16DEV   FP32 arithmetic; per node one FP32 scale phi_s and 27 FP16
+ *                     relative deviations q_i, g_i = W_i phi_s (P_i(u) + q_i).
+ *   ELBM_F32_BF16DEV  as above with BF16 deviations.
+ * Reductions (mass, entropy) always accumulate in FP64. */
+typedef enum { ELBM_F64 = 0, ELBM_F32 = 1, ELBM_F32_F16DEV = 2, ELBM_F32_BF16DEV = 3 } elbm_precision;
+
+/* Element type of caller arrays handed to read/write calls. */
+typedef enum { ELBM_DTYPE_F64 = 0, ELBM_DTYPE_F32 = 1 } elbm_dtype;
+
+/* Boundaries.  dirichlet_x = 0: periodic in x, y, z.  dirichlet_x = 1: x faces
+ * held at phi_lo (wall at x = -1/2) and phi_hi (wall at x = Nx - 1/2) by
+ * anti-bounce-back, g_i(x_b) = -g*_opp(i)(x_b) + 2 W_i phi_w (wall velocity 0);
+ * y and z stay periodic.  (Section 4.2.1 names the faces but gives no scheme.) */
+typedef struct {
+    int32_t dirichlet_x;
+    double phi_lo;
+    double phi_hi;
+} elbm_bc;
+
+/* Run-time parameters (defaults in brackets).
+ *   theta     stabilizer guard: lambda = 1 where <dh|dh>_H <= theta^2 phi
+ *             [1e-8 for ELBM_F64, 3e-4 otherwise]; "if dh = 0 set lambda = 1",
+ *             Eq. (method-lambda), given a threshold.
+ *   eps       positivity threshold of Eq. (method-alpha) [0].
+ *   fallback  1 = positivity fallback on [1]. */
+typedef struct {
+    double theta;
+    double eps;
+    int32_t fallback;
+} elbm_params;
+
+typedef struct elbm_ctx* elbm_handle;
+
+/* ---------------------------------------------------------------- lifecycle */
+
+/* Create a lattice of dims[0] x dims[1] x dims[2] = Nx x Ny x Nz nodes (each >= 1,
+ * total 27 N < 2^31 per population buffer index space) in precision `prec`,
+ * boundaries `bc` (NULL = fully periodic), work ordered on `cuda_stream`
+ * (a cudaStream_t, NULL = default stream).  Allocates two population buffers
+ * (A/B) on the current device.  Initial tensor: D = 0 is not allowed, so a
+ * tensor must be set before the first step; velocity 0; no source.
+ * Errors: ELBM_ERR_ARG, ELBM_ERR_OOM, ELBM_ERR_CUDA. */
+elbm_status elbm_create(const int64_t dims[3], elbm_precision prec, const elbm_bc* bc,
+                        void* cuda_stream, elbm_handle* out);
+
+/* Free every device buffer of the handle (after synchronising its stream). */
+void elbm_destroy(elbm_handle h);
+
+/* Message of the last failing call on `h` ("" if none); valid until the next call. */
+const char* elbm_last_error(elbm_handle h);
+
+/* Name of a status code. */
+const char* elbm_status_string(elbm_status s);
+
+/* Set theta, eps, fallback (see elbm_params).  ELBM_ERR_ARG if theta < 0. */
+elbm_status elbm_set_params(elbm_handle h, const elbm_params* p);
+
+/* --------------------------------------------------------- problem data */
+
+/* Uniform tensor D, 6 doubles (Dxx, Dxy, Dxz, Dyy, Dyz, Dzz), host memory.
+ * Derives S = (I/2 + 3 D)^-1 (Eq. method-s-from-d) in FP64 on the host and keeps
+ * T = 2I - S = 12 D (I + 6 D)^-1, which holds weak-axis diffusivities to full
+ * relative precision in FP32.  ELBM_ERR_NOT_SPD unless D is SPD. */
+elbm_status elbm_set_tensor_uniform(elbm_handle h, const double D6[6]);
+
+/* Per-node tensor, FP32 [6][N] in the same component order, host or device.
+ * A device pre-pass converts it once to the per-node T field (FP32 [6][N],
+ * kept by the library).  Nodes whose D is not SPD make the call fail with
+ * ELBM_ERR_NOT_SPD (checked on the device). */
+elbm_status elbm_set_tensor_field(elbm_handle h, const float* D6);
+
+/* Per-node tensor from parameters theta, FP32 [6][N], host or device:
+ * theta[0..2] = ln d1, ln d2, ln d3 (principal diffusivities), theta[3..5] =
+ * ZYZ Euler angles (a, b, c) in radians, D = Rz(a) Ry(b) Rz(c) diag(d) R^T
+ * (Sections 2.3 and 3.1).  Converted once to the T field on the device. */
+elbm_status elbm_set_tensor_params_field(elbm_handle h, const float* theta6);
+
+/* Uniform velocity u (3 doubles, host).  ELBM_ERR_MACH unless every
+ * P_i(u) = 1 + 3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u > 0.  For the deviation
+ * storages the velocity is also the reference of the stored deviations, so it
+ * may only be changed before elbm_init_* (else ELBM_ERR_STATE). */
+elbm_status elbm_set_velocity_uniform(elbm_handle h, const double u[3]);
+
+/* Time-constant volumetric source R, FP32 [N], host or device, or NULL to
+ * remove it.  Applied by the Strang split S(1/2) -> collide-stream -> S(1/2),
+ * g_i += (1/2) R E_i(u) with E_i(u) = W_i P_i(u) (Section 3.3); the two
+ * half-steps between consecutive steps are merged into one full step. */
+elbm_status elbm_set_source(elbm_handle h, const float* R);
+
+/* --------------------------------------------------------------- state */
+
+/* Initial state g = g_eq(phi0, u) (initial populations are not stated in the
+ * paper; the equilibrium start is this library's reading).  phi0 is [N] of
+ * `dtype`, host or device.  Resets the step counter and the fallback count. */
+elbm_status elbm_init_equilibrium(elbm_handle h, const void* phi0, elbm_dtype dtype);
+
+/* Set the state from pre-collision populations g [27][N] of `dtype` (host or
+ * device): the populations that the next step collides, after the trailing
+ * source half-step of the previous step.  For the deviation storages the
+ * values are rounded to the storage format. */
+elbm_status elbm_write_populations(elbm_handle h, const void* g, elbm_dtype dtype);
+
+/* Read the current pre-collision populations g [27][N] into `out` (host or
+ * device) as `dtype`.  Synchronises the stream when `out` is host memory. */
+elbm_status elbm_read_populations(elbm_handle h, void* out, elbm_dtype dtype);
+
+/* Read phi = sum_i g_i [N] and, if q_out != NULL, the LB diffusive flux
+ * q = j - S j / 2 [3][N] (Eq. app-cube-lb-flux) of the current state.
+ * Buffers host or device of `dtype`. */
+elbm_status elbm_read_moments(elbm_handle h, void* phi_out, void* q_out, elbm_dtype dtype);
+
+/* Advance `nsteps` >= 0 collide-stream steps (asynchronous on the stream). */
+elbm_status elbm_step(elbm_handle h, int64_t nsteps);
+
+/* Conservation diagnostics of the current state, FP64 (host pointers, any may
+ * be NULL): mass = sum_x phi, entropy = sum_x sum_i g_i ln(g_i/W_i) over
+ * positive g_i (Eq. method-entropy), gmin = min g_i, n_fallback = node
+ * collisions that took the positivity fallback since the last init.
+ * Deterministic (fixed-order two-pass reduction).  Returns ELBM_ERR_NONFINITE
+ * (values still written) if any population is NaN or infinite. */
+elbm_status elbm_reduce(elbm_handle h, double* mass, double* entropy, double* gmin,
+                        int64_t* n_fallback);
+
+/* Steps taken since the last init. */
+elbm_status elbm_get_step(elbm_handle h, int64_t* step);
+
+/* Wait for the handle's stream; report asynchronous CUDA errors. */
+elbm_status elbm_synchronize(elbm_handle h);
+
+/* Checkpoints: byte size of a snapshot (populations in storage format + step
+ * counter + fallback count), save into / load from a caller buffer (host or
+ * device) of at least that size.  A snapshot is only valid for a handle of the
+ * same dims and precision. */
+elbm_status elbm_checkpoint_size(elbm_handle h, size_t* bytes);
+elbm_status elbm_checkpoint_save(elbm_handle h, void* buf, size_t bytes);
+elbm_status elbm_checkpoint_load(elbm_handle h, const void* buf, size_t bytes);
+
+/* Device pointers of the current population buffer and (deviation storages)
+ * of its FP32 scale plane, for profiling and zero-copy inspection.  They change
+ * after every step (A/B swap).  Owned by the library. */
+elbm_status elbm_state_pointers(elbm_handle h, void** pops, void** scale);
+
+/* ------------------------------------------------ host-only validation (no GPU) */
+
+/* ELBM_OK if D6 is SPD, else ELBM_ERR_NOT_SPD. */
+elbm_status elbm_check_tensor(const double D6[6]);
+
+/* ELBM_OK if P_i(u) > 0 for all i, else ELBM_ERR_MACH. */
+elbm_status elbm_check_velocity(const double u[3]);
+
+/* T = 2I - S (6 doubles) of an SPD D6, computed in FP64 on the host. */
+elbm_status elbm_relaxation_complement(const double D6[6], double T6_out[6]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ELBM_H */

@@ -1,0 +1,144 @@
+// Per-node collision of the anisotropic ADE entropic LBM (Sections 2.2-2.6),
+// evaluated in registers on 27 pre-collision populations.
+//
+// With phi = sum g, j = sum c g - phi u, a = (I - S) j = T j - j (T = 2I - S),
+// g_eq_i = phi E_i (E_i = W_i P_i(u)), ds_i = 3 W_i c_i.j, dh_i = g_i - g_eq_i - ds_i,
+// the collision of Eq. (method-collision) with amplitude lambda = 1 + kappa is
+//     g*_i = g_eq_i + 3 W_i c_i.a - kappa dh_i
+//          = (1 + kappa) phi E_i - kappa g_i + 3 W_i c_i.(a + kappa j).
+// kappa = lambda - 1 from Eqs. (method-lambda, method-correction) with the terms
+// that vanish identically (sum dh = 0, sum c dh = 0) removed:
+//     kappa = [sum dh_i K3_i c_i.a + phi sum dh_i L_i] / [sum dh_i^2 M_i],
+//     K3_i = 3 (1/P_i - 1), L_i = ln P_i - 3 c_i.u + 1.5 u.u, M_i = 1/(W_i P_i),
+// and kappa = 0 where u = 0 (both numerator terms vanish identically), where
+// sum dh_i^2 M_i <= theta^2 phi^2 (i.e. <dh|dh>_H <= theta^2 phi), or phi <= 0.
+// The positivity fallback (Eq. method-alpha) shortens g* - g when some g*_i < eps.
+#pragma once
+#include "lattice.cuh"
+
+namespace elbm {
+
+// Per-population constants that depend on the uniform velocity (host-computed in FP64).
+template <typename R>
+struct PopConsts {
+  R E[Q];    // W_i P_i(u)
+  R K3[Q];   // 3 (1/P_i(u) - 1)
+  R L[Q];    // ln P_i(u) - 3 c_i.u + 1.5 u.u
+  R M[Q];    // 1 / (W_i P_i(u))
+  R ux, uy, uz;
+  R theta2;  // theta^2
+  R eps;
+  R phi_lo, phi_hi;  // Dirichlet wall values
+  Sym6<R> T;         // uniform T = 2I - S
+};
+
+// c_i . v for all 27 velocities from 9 (cy, cz) partial sums.
+template <typename R>
+struct Dots {
+  R d[Q];
+  __device__ __forceinline__ Dots(R vx, R vy, R vz) {
+    R yz[9];
+#pragma unroll
+    for (int cy = -1; cy <= 1; ++cy)
+#pragma unroll
+      for (int cz = -1; cz <= 1; ++cz) {
+        R t = cy == 0 ? R(0) : (cy > 0 ? vy : -vy);
+        yz[3 * (cy + 1) + (cz + 1)] = cz == 0 ? t : (cz > 0 ? t + vz : t - vz);
+      }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const R t = yz[i % 9];
+      d[i] = cx_of(i) == 0 ? t : (cx_of(i) > 0 ? t + vx : t - vx);
+    }
+  }
+};
+
+// phi and the first moment sum_i c_i g_i, by partial sums over cz, then cy.
+template <typename R>
+__device__ __forceinline__ void moments(const R (&g)[Q], R& phi, R& mx, R& my, R& mz) {
+  R s[9], dz[9];
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    s[p] = g[3 * p] + g[3 * p + 1] + g[3 * p + 2];
+    dz[p] = g[3 * p + 2] - g[3 * p];
+  }
+  R t[3], e[3];
+#pragma unroll
+  for (int cx = 0; cx < 3; ++cx) {
+    t[cx] = s[3 * cx] + s[3 * cx + 1] + s[3 * cx + 2];
+    e[cx] = s[3 * cx + 2] - s[3 * cx];
+  }
+  phi = t[0] + t[1] + t[2];
+  mx = t[2] - t[0];
+  my = e[0] + e[1] + e[2];
+  mz = (dz[0] + dz[1] + dz[2]) + (dz[3] + dz[4] + dz[5]) + (dz[6] + dz[7] + dz[8]);
+}
+
+// VEL = 0: u = 0 exactly (kappa = 0); VEL = 1: uniform u from PopConsts.
+// Returns true if the positivity fallback was taken.
+template <typename R, int VEL>
+__device__ __forceinline__ bool collide_node(R (&g)[Q], const Sym6<R>& T, const PopConsts<R>& k,
+                                             bool fallback) {
+  R phi, mx, my, mz;
+  moments(g, phi, mx, my, mz);
+  R jx = mx, jy = my, jz = mz;
+  if (VEL == 1) {
+    jx = mx - phi * k.ux;
+    jy = my - phi * k.uy;
+    jz = mz - phi * k.uz;
+  }
+  R tx, ty, tz;
+  sym_mul(T, jx, jy, jz, tx, ty, tz);
+  const R ax = tx - jx, ay = ty - jy, az = tz - jz;  // (I - S) j
+  R gs[Q];
+  if (VEL == 0) {
+    const Dots<R> ca(ax, ay, az);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) gs[i] = phi * R(w_of(i)) + R(3.0 * w_of(i)) * ca.d[i];
+  } else {
+    R kappa = R(0);
+    {
+      const Dots<R> cj(jx, jy, jz);
+      const Dots<R> ca(ax, ay, az);
+      R num = R(0), den = R(0);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        R dh = g[i] - phi * k.E[i];
+        dh = dh - R(3.0 * w_of(i)) * cj.d[i];
+        num += dh * (k.K3[i] * ca.d[i] + phi * k.L[i]);
+        den += dh * (dh * k.M[i]);
+      }
+      if (phi > R(0) && den > k.theta2 * phi * phi) kappa = num / den;
+    }
+    const R psi = (R(1) + kappa) * phi;
+    const Dots<R> cb(ax + kappa * jx, ay + kappa * jy, az + kappa * jz);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) gs[i] = psi * k.E[i] - kappa * g[i] + R(3.0 * w_of(i)) * cb.d[i];
+  }
+  bool took = false;
+  if (fallback) {
+    R mn = gs[0];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) mn = mn < gs[i] ? mn : gs[i];
+    if (mn < k.eps) {
+      took = true;
+      R alpha = R(1);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const R om = gs[i] - g[i];
+        if (om < R(0)) {
+          const R r = (g[i] - k.eps) / (-om);
+          alpha = r < alpha ? r : alpha;
+        }
+      }
+      alpha = alpha > R(0) ? alpha : R(0);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) gs[i] = g[i] + alpha * (gs[i] - g[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < Q; ++i) g[i] = gs[i];
+  return took;
+}
+
+}  // namespace elbm

@@ -1,0 +1,53 @@
+// Launch interfaces between the C ABI (api.cu) and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "collide.cuh"
+
+namespace elbm {
+
+struct StepLaunch {
+  int prec;                     // elbm_precision
+  int vel;                      // 0: u = 0, 1: uniform u
+  int nx, ny, nz;
+  size_t N;
+  int dirichlet, fallback;
+  const void* pin;              // post-collision populations (storage elements)
+  const float* sin;             // deviation scale plane in
+  void* pout;
+  float* sout;
+  const float* T6;              // per-node T = 2I - S [6][N] or null (uniform T in consts)
+  const float* src;             // per-node source [N] or null
+  unsigned long long* counters; // [0] fallback count
+  const PopConsts<double>* kd;  // host copies, passed by value to the kernel
+  const PopConsts<float>* kf;
+};
+cudaError_t launch_step(const StepLaunch& L, cudaStream_t s);
+
+// State transfer.  mode 0: populations [27][N] <-> caller; mode 1: phi0 [N] -> equilibrium.
+struct StateIO {
+  int prec, nx, ny, nz;
+  size_t N;
+  int dirichlet;
+  void* pops;                   // storage buffer (read: const)
+  float* scale;
+  const float* T6;
+  const float* src;
+  const PopConsts<double>* kd;
+  const PopConsts<float>* kf;
+};
+cudaError_t launch_write_state(const StateIO& S, const void* in, int in_f32, int from_phi, cudaStream_t s);
+// what: 0 = populations [27][N]; 1 = phi [N] and optional q [3][N]
+cudaError_t launch_read_state(const StateIO& S, void* out, void* q_out, int out_f32, int what, cudaStream_t s);
+// partials: scratch of >= reduce_blocks(N) * 4 doubles; out4: device (mass, entropy, gmin, nonfinite count)
+size_t reduce_blocks(const StateIO& S);
+cudaError_t launch_reduce(const StateIO& S, double* scratch, double* out4, cudaStream_t s);
+
+// Tensor pre-pass: D6 or theta6 (float [6][N]) -> T6 (float [6][N]); bad_count counts non-SPD nodes.
+cudaError_t launch_tensor_prepass(const float* in, int is_params, float* T6, size_t N,
+                                  unsigned long long* bad_count, cudaStream_t s);
+
+}  // namespace elbm

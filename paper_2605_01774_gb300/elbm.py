@@ -1,0 +1,275 @@
+"""ctypes binding of include/elbm.h: same names, argument marshalling only.
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays; they are passed to
+the library as raw pointers (device or host), which the library tells apart.
+Every call raises :class:`ElbmError` on a non-OK status.  Nothing here
+computes any part of the method.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB
+
+ELBM_F64, ELBM_F32, ELBM_F32_F16DEV, ELBM_F32_BF16DEV = 0, 1, 2, 3
+ELBM_DTYPE_F64, ELBM_DTYPE_F32 = 0, 1
+PRECISIONS = {"f64": ELBM_F64, "f32": ELBM_F32, "f16dev": ELBM_F32_F16DEV, "bf16dev": ELBM_F32_BF16DEV}
+
+STATUS = ["ELBM_OK", "ELBM_ERR_ARG", "ELBM_ERR_NOT_SPD", "ELBM_ERR_MACH", "ELBM_ERR_OOM", "ELBM_ERR_CUDA",
+          "ELBM_ERR_NONFINITE", "ELBM_ERR_TIMEOUT", "ELBM_ERR_STATE", "ELBM_ERR_UNSUPPORTED"]
+
+
+class ElbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS[status] if 0 <= status < len(STATUS) else status}: {msg}")
+        self.status = status
+
+
+class elbm_bc(C.Structure):
+    _fields_ = [("dirichlet_x", C.c_int32), ("phi_lo", C.c_double), ("phi_hi", C.c_double)]
+
+
+class elbm_params(C.Structure):
+    _fields_ = [("theta", C.c_double), ("eps", C.c_double), ("fallback", C.c_int32)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libelbm.so (built by paper_2605_01774_gb300.build); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise ImportError(f"{LIB} is not built; run `python -m paper_2605_01774_gb300.build` "
+                          "(the CUDA library is required, there is no CPU path)")
+    L = C.CDLL(LIB)
+    H, S, P, I64 = C.c_void_p, C.c_int, C.c_void_p, C.c_int64
+    D = C.POINTER(C.c_double)
+    sig = {
+        "elbm_create": (S, [C.POINTER(C.c_int64), S, C.POINTER(elbm_bc), P, C.POINTER(H)]),
+        "elbm_destroy": (None, [H]),
+        "elbm_last_error": (C.c_char_p, [H]),
+        "elbm_status_string": (C.c_char_p, [S]),
+        "elbm_set_params": (S, [H, C.POINTER(elbm_params)]),
+        "elbm_set_tensor_uniform": (S, [H, D]),
+        "elbm_set_tensor_field": (S, [H, P]),
+        "elbm_set_tensor_params_field": (S, [H, P]),
+        "elbm_set_velocity_uniform": (S, [H, D]),
+        "elbm_set_source": (S, [H, P]),
+        "elbm_init_equilibrium": (S, [H, P, S]),
+        "elbm_write_populations": (S, [H, P, S]),
+        "elbm_read_populations": (S, [H, P, S]),
+        "elbm_read_moments": (S, [H, P, P, S]),
+        "elbm_step": (S, [H, I64]),
+        "elbm_reduce": (S, [H, D, D, D, C.POINTER(C.c_int64)]),
+        "elbm_get_step": (S, [H, C.POINTER(C.c_int64)]),
+        "elbm_synchronize": (S, [H]),
+        "elbm_checkpoint_size": (S, [H, C.POINTER(C.c_size_t)]),
+        "elbm_checkpoint_save": (S, [H, P, C.c_size_t]),
+        "elbm_checkpoint_load": (S, [H, P, C.c_size_t]),
+        "elbm_state_pointers": (S, [H, C.POINTER(P), C.POINTER(P)]),
+        "elbm_check_tensor": (S, [D]),
+        "elbm_check_velocity": (S, [D]),
+        "elbm_relaxation_complement": (S, [D, D]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a) -> C.c_void_p:
+    """Raw pointer of a contiguous torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return C.c_void_p(0)
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return C.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr())
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _dtype_code(a) -> int:
+    name = str(a.dtype)
+    if name.endswith("float64"):
+        return ELBM_DTYPE_F64
+    if name.endswith("float32"):
+        return ELBM_DTYPE_F32
+    raise TypeError(f"dtype {a.dtype} not supported (float64 or float32)")
+
+
+def _d(vals, n) -> C.Array:
+    vals = [float(v) for v in np.asarray(vals, dtype=np.float64).ravel()]
+    if len(vals) != n:
+        raise ValueError(f"expected {n} values")
+    return (C.c_double * n)(*vals)
+
+
+def _check(status: int, h=None):
+    if status != 0:
+        msg = lib().elbm_last_error(h).decode() if h else ""
+        raise ElbmError(status, msg)
+
+
+def _stream_ptr(stream) -> C.c_void_p:
+    if stream is None:
+        return C.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+# --------------------------------------------------------------------- API
+def elbm_create(dims, prec="f32", bc=None, stream=None):
+    d = (C.c_int64 * 3)(*[int(v) for v in dims])
+    p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    b = None
+    if bc is not None:
+        b = C.byref(elbm_bc(1, float(bc[0]), float(bc[1])))
+    h = C.c_void_p()
+    _check(lib().elbm_create(d, p, b, _stream_ptr(stream), C.byref(h)))
+    return h
+
+
+def elbm_destroy(h):
+    lib().elbm_destroy(h)
+
+
+def elbm_set_params(h, theta, eps=0.0, fallback=True):
+    _check(lib().elbm_set_params(h, C.byref(elbm_params(float(theta), float(eps), int(bool(fallback))))), h)
+
+
+def elbm_set_tensor_uniform(h, D6):
+    _check(lib().elbm_set_tensor_uniform(h, _d(D6, 6)), h)
+
+
+def elbm_set_tensor_field(h, D6):
+    _check(lib().elbm_set_tensor_field(h, _ptr(D6)), h)
+
+
+def elbm_set_tensor_params_field(h, theta6):
+    _check(lib().elbm_set_tensor_params_field(h, _ptr(theta6)), h)
+
+
+def elbm_set_velocity_uniform(h, u):
+    _check(lib().elbm_set_velocity_uniform(h, _d(u, 3)), h)
+
+
+def elbm_set_source(h, R):
+    _check(lib().elbm_set_source(h, _ptr(R)), h)
+
+
+def elbm_init_equilibrium(h, phi0):
+    _check(lib().elbm_init_equilibrium(h, _ptr(phi0), _dtype_code(phi0)), h)
+
+
+def elbm_write_populations(h, g):
+    _check(lib().elbm_write_populations(h, _ptr(g), _dtype_code(g)), h)
+
+
+def elbm_read_populations(h, out):
+    _check(lib().elbm_read_populations(h, _ptr(out), _dtype_code(out)), h)
+    return out
+
+
+def elbm_read_moments(h, phi_out, q_out=None):
+    _check(lib().elbm_read_moments(h, _ptr(phi_out), _ptr(q_out), _dtype_code(phi_out)), h)
+    return phi_out, q_out
+
+
+def elbm_step(h, nsteps=1):
+    _check(lib().elbm_step(h, int(nsteps)), h)
+
+
+def elbm_reduce(h, allow_nonfinite=False):
+    m, e, g = C.c_double(), C.c_double(), C.c_double()
+    n = C.c_int64()
+    s = lib().elbm_reduce(h, C.byref(m), C.byref(e), C.byref(g), C.byref(n))
+    if s != 0 and not (allow_nonfinite and s == 6):
+        _check(s, h)
+    return dict(mass=m.value, entropy=e.value, gmin=g.value, n_fallback=n.value, status=s)
+
+
+def elbm_get_step(h):
+    v = C.c_int64()
+    _check(lib().elbm_get_step(h, C.byref(v)), h)
+    return v.value
+
+
+def elbm_synchronize(h):
+    _check(lib().elbm_synchronize(h), h)
+
+
+def elbm_checkpoint_size(h):
+    v = C.c_size_t()
+    _check(lib().elbm_checkpoint_size(h, C.byref(v)), h)
+    return v.value
+
+
+def elbm_checkpoint_save(h, buf):
+    _check(lib().elbm_checkpoint_save(h, _ptr(buf), buf.numel() * buf.element_size() if hasattr(buf, "numel")
+                                      else buf.nbytes), h)
+
+
+def elbm_checkpoint_load(h, buf):
+    _check(lib().elbm_checkpoint_load(h, _ptr(buf), buf.numel() * buf.element_size() if hasattr(buf, "numel")
+                                      else buf.nbytes), h)
+
+
+def elbm_state_pointers(h):
+    p, s = C.c_void_p(), C.c_void_p()
+    _check(lib().elbm_state_pointers(h, C.byref(p), C.byref(s)), h)
+    return p.value, s.value
+
+
+def elbm_check_tensor(D6) -> int:
+    return lib().elbm_check_tensor(_d(D6, 6))
+
+
+def elbm_check_velocity(u) -> int:
+    return lib().elbm_check_velocity(_d(u, 3))
+
+
+def elbm_relaxation_complement(D6):
+    out = (C.c_double * 6)()
+    _check(lib().elbm_relaxation_complement(_d(D6, 6), out))
+    return np.array(list(out))
+
+
+# ------------------------------------------------------------ convenience
+class Lattice:
+    """Owning wrapper over one handle (marshalling only)."""
+
+    def __init__(self, dims, prec="f32", bc=None, stream=None):
+        self.dims = tuple(int(v) for v in dims)
+        self.N = self.dims[0] * self.dims[1] * self.dims[2]
+        self.prec = prec
+        self.h = elbm_create(self.dims, prec, bc, stream)
+
+    def close(self):
+        if self.h is not None:
+            elbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
