@@ -1,0 +1,379 @@
+"""Throughput of the fused ELBM-ADE step on the advected anisotropic Gaussian
+plume (256^3 periodic, u = (0.05, 0.03, 0.02), D = R diag(0.1, 1e-3, 1e-5) R^T,
+sigma0 = 8), in MLUPS and as a fraction of the measured HBM bandwidth.
+
+One step = one collide-stream pass over the whole lattice.  The headline form
+is FP32 arithmetic with FP16 deviation storage; the plain FP32 form, the BF16
+deviation form and FP64 are measured beside it, each with its relative L2
+error of phi against the FP64 form after a fixed number of steps (the FP64
+form itself matches the FP64 oracle to 1e-12 in the parity tests).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank steps its own replica of the
+lattice (the method has no data-path exchange for independent problems), and
+`value` is the node updates of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "ELBM-ADE MLUPS & % HBM roofline, chosen vs plain form at stated L2 error"
+UNIT = "MLUPS"
+BYTES_PER_NODE = {"f64": 27 * 8 * 2, "f32": 27 * 4 * 2, "f16dev": (27 * 2 + 4) * 2, "bf16dev": (27 * 2 + 4) * 2}
+WORKLOAD = ("advected anisotropic Gaussian plume 256^3 periodic, u=(0.05,0.03,0.02), "
+            "D=R diag(0.1,1e-3,1e-5) R^T (seeded ZYZ, seed 2), sigma0=8")
+KERNEL_SOURCES = ["collide.cuh", "storage.cuh", "pull.cuh", "step.cu", "lattice.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2605_01774_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)"
+    return 6800.0, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+
+
+def ncu_traffic(form: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on the current kernel."""
+    p = os.path.join(ROOT, "profiles", "step_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    e = d.get("forms", {}).get(form)
+    return None if e is None else float(e["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.device = device
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.device)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2][k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(v: float, dist, device=None) -> float:
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v: float, dist, device=None) -> float:
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local, dist):
+    import torch
+
+    from paper_2605_01774_gb300 import elbm as E
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    E.lib()
+    wl = synth.gaussian_plume(n=args.size)
+    D6 = synth.d6_from_matrix(wl.D)
+    N = int(np.prod(wl.dims))
+    stream = torch.cuda.Stream(device=dev)
+    phi0 = torch.as_tensor(wl.phi0, dtype=torch.float32, device=dev)
+
+    def make(prec):
+        lat = E.Lattice(wl.dims, prec, stream=stream)
+        E.elbm_set_tensor_uniform(lat.h, D6)
+        E.elbm_set_velocity_uniform(lat.h, wl.u)
+        stream.wait_stream(torch.cuda.current_stream(dev))
+        E.elbm_init_equilibrium(lat.h, phi0)
+        return lat
+
+    def timed(lat, K, W, sample_clocks=False):
+        E.elbm_step(lat.h, W)
+        stream.synchronize()
+        barrier(dist)
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(local) if sample_clocks else None
+        if sampler:
+            sampler.__enter__()
+        ev0.record(stream)
+        E.elbm_step(lat.h, K)
+        ev1.record(stream)
+        ev1.synchronize()
+        if sampler:
+            sampler.__exit__(None, None, None)
+        torch.cuda.synchronize(dev)
+        barrier(dist)
+        ms = ev0.elapsed_time(ev1)
+        return ms, (sampler.summary() if sampler else None)
+
+    forms = {}
+    headline = args.form
+    order = [headline] + [f for f in ("f32", "bf16dev", "f16dev") if f != headline]
+    clocks = None
+    for prec in order:
+        lat = make(prec)
+        ms, ck = timed(lat, args.steps, args.warmup, sample_clocks=(prec == headline))
+        if prec == headline:
+            clocks = ck
+        d = E.elbm_reduce(lat.h, allow_nonfinite=True)
+        lat.close()
+        ms_max = max_over_ranks(ms, dist, dev)
+        forms[prec] = dict(ms_per_step=ms_max / args.steps,
+                           mlups=world * N * args.steps / (ms_max * 1e-3) / 1e6,
+                           bytes_per_node=BYTES_PER_NODE[prec], n_fallback=d["n_fallback"])
+    # FP64: ALU-bound on this part; fewer steps keep the run short
+    k64 = max(10, min(args.steps, 200))
+    lat = make("f64")
+    ms, _ = timed(lat, k64, min(args.warmup, 3))
+    lat.close()
+    ms = max_over_ranks(ms, dist, dev)
+    forms["f64"] = dict(ms_per_step=ms / k64, mlups=world * N * k64 / (ms * 1e-3) / 1e6,
+                        bytes_per_node=BYTES_PER_NODE["f64"], steps=k64)
+
+    # accuracy: phi after `ek` steps of each form vs the FP64 form (parity-tested against the oracle)
+    ek = args.err_steps
+    phis = {}
+    for prec in ["f64"] + order:
+        lat = make(prec)
+        E.elbm_step(lat.h, ek)
+        out = torch.empty(wl.dims[::-1], dtype=torch.float64, device=dev)
+        with torch.cuda.stream(stream):
+            E.elbm_read_moments(lat.h, out)
+        stream.synchronize()
+        phis[prec] = out
+        lat.close()
+    ref = phis["f64"]
+    for prec in order:
+        forms[prec]["rel_l2_phi_vs_fp64"] = float(torch.linalg.vector_norm(phis[prec] - ref) /
+                                                  torch.linalg.vector_norm(ref))
+        forms[prec]["rel_linf_phi_vs_fp64"] = float((phis[prec] - ref).abs().max() / ref.abs().max())
+    del phis, ref
+
+    # end to end through the C ABI with host buffers: upload phi0, K steps, read phi back
+    host_phi0 = torch.as_tensor(wl.phi0, dtype=torch.float32).pin_memory()
+    host_out = torch.empty(wl.dims[::-1], dtype=torch.float32).pin_memory()
+    lat = E.Lattice(wl.dims, headline, stream=stream)
+    E.elbm_set_tensor_uniform(lat.h, D6)
+    E.elbm_set_velocity_uniform(lat.h, wl.u)
+    E.elbm_init_equilibrium(lat.h, host_phi0)
+    E.elbm_step(lat.h, args.warmup)
+    stream.synchronize()
+    barrier(dist)
+    t0 = time.perf_counter()
+    E.elbm_init_equilibrium(lat.h, host_phi0)
+    E.elbm_step(lat.h, args.steps)
+    E.elbm_read_moments(lat.h, host_out)
+    mass = E.elbm_reduce(lat.h, allow_nonfinite=True)["mass"]
+    t_e2e = time.perf_counter() - t0
+    lat.close()
+    t_e2e = max_over_ranks(t_e2e, dist, dev)
+    e2e = dict(value=world * N * args.steps / t_e2e / 1e6, unit=UNIT,
+               h2d_bytes_per_step=N * 4 / args.steps, d2h_bytes_per_step=(N * 4 + 8 * 4) / args.steps,
+               final_mass=mass)
+
+    if rank != 0:
+        return None
+    peak, peak_src = measured_peaks()
+    hf = forms[headline]
+    achieved = hf["bytes_per_node"] * N / (hf["ms_per_step"] * 1e-3) / 1e9
+    traffic = ncu_traffic(headline)
+    for prec in order + ["f64"]:
+        f = forms[prec]
+        f["achieved_gbs"] = f["bytes_per_node"] * N / (f["ms_per_step"] * 1e-3) / 1e9
+        f["hbm_frac_of_measured"] = f["achieved_gbs"] / peak
+    line = {
+        "metric": METRIC, "value": hf["mlups"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": hf["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 compute, f16 deviation storage"
+        if headline == "f16dev" else headline, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": N, "form": headline, "plain_form": "f32",
+                   "l2_flush": "inputs larger than L2: %.2f GB per population buffer" %
+                               (hf["bytes_per_node"] / 2 * N / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "err_steps": ek},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                     "algorithmic_bytes_per_node": hf["bytes_per_node"], "kernel": "k_step"},
+        "forms": forms,
+        "chosen_vs_plain_speedup": hf["mlups"] / forms["f32"]["mlups"],
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    return line
+
+
+# ------------------------------------------------------------------------ oracle arm
+def oracle_sample(n=40):
+    """The bench workload's physics (u, D, sigma0) on a bounded n^3 periodic sample."""
+    return synth.gaussian_plume(n=n)
+
+
+def cpu_baseline(args, seconds=15.0):
+    import torch
+
+    import oracle as O
+    wl = oracle_sample(args.cpu_sample)
+    prob = O.Problem.from_tensor(wl.u, wl.D, theta=3e-4, lam_mode="literal")
+    g = O.init_equilibrium(wl.phi0, wl.u)
+    g = O.step(g, prob, 0)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        g = O.step(g, prob, n)
+        n += 1
+    dt = time.perf_counter() - t0
+    N = int(np.prod(wl.dims))
+    return {"value": N * n / dt / 1e6, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{n} steps of the bench physics on a {wl.dims[0]}^3 periodic box (FP64, torch CPU)"}
+
+
+def run_reference(args, rank, world, dist):
+    import torch
+
+    import oracle as O
+    if rank != 0:
+        return None
+    wl = oracle_sample(args.cpu_sample)
+    prob = O.Problem.from_tensor(wl.u, wl.D, theta=3e-4, lam_mode="literal")
+    g = O.init_equilibrium(wl.phi0, wl.u)
+    for k in range(args.warmup):
+        g = O.step(g, prob, k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        g = O.step(g, prob, args.warmup + k)
+    dt = time.perf_counter() - t0
+    N = int(np.prod(wl.dims))
+    v = N * args.steps / dt / 1e6
+    sample = f"{args.steps} steps of the bench physics on a {wl.dims[0]}^3 periodic box (FP64 oracle, torch CPU)"
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="f16dev", choices=["f16dev", "bf16dev", "f32"])
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--err-steps", type=int, default=200)
+    ap.add_argument("--cpu-sample", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        # the oracle runs on the host cores of rank 0 only; other ranks exit without work
+        rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+        line = run_reference(args, rank, world, None)
+        if rank == 0 and line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    rank, world, local, dist = dist_setup(args.gpus)
+    if True:
+        line = run_ours(args, rank, world, local, dist)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

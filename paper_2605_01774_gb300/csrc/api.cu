@@ -20,7 +20,7 @@ struct elbm_ctx {
   void* pops[2] = {nullptr, nullptr};
   float* scale[2] = {nullptr, nullptr};
   int cur = 0;
-  float* T6 = nullptr;       // per-node T field (owned)
+  void* T6 = nullptr;        // per-node T field (owned; double for FP64, else float)
   float* src = nullptr;      // per-node source (owned)
   bool have_tensor = false;
   bool tensor_field = false;
@@ -298,13 +298,15 @@ elbm_status elbm_set_tensor_uniform(elbm_handle h, const double D6[6]) {
 
 static elbm_status set_field(elbm_handle h, const float* in, int is_params) {
   if (!h || !in) return fail(h, ELBM_ERR_ARG, "null argument");
-  if (!h->T6) CK(cudaMalloc((void**)&h->T6, 6 * h->N * sizeof(float)), "cudaMalloc T6");
+  const size_t tb = h->prec == 0 ? sizeof(double) : sizeof(float);
+  if (!h->T6) CK(cudaMalloc(&h->T6, 6 * h->N * tb), "cudaMalloc T6");
   const void* dev;
   void* tmp;
   elbm_status s = to_device(h, in, 6 * h->N * sizeof(float), &dev, &tmp);
   if (s != ELBM_OK) return s;
   CK(cudaMemsetAsync(h->d_counters + 1, 0, sizeof(unsigned long long), h->stream), "memset");
-  CK(launch_tensor_prepass(static_cast<const float*>(dev), is_params, h->T6, h->N, h->d_counters + 1, h->stream),
+  CK(launch_tensor_prepass(static_cast<const float*>(dev), is_params, h->T6, h->prec == 0, h->N, h->d_counters + 1,
+                           h->stream),
      "tensor pre-pass");
   unsigned long long bad = 0;
   CK(cudaMemcpyAsync(&bad, h->d_counters + 1, sizeof(bad), cudaMemcpyDeviceToHost, h->stream), "memcpy");

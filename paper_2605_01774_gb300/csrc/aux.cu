@@ -65,7 +65,8 @@ k_write(Elem* __restrict__ pops, float* __restrict__ scale, Grid G, const void* 
 // ----------------------------------------------------------------- read state
 template <typename Elem, typename Tout, int WHAT>
 __global__ void __launch_bounds__(256)
-k_read(Field<Elem> f, Grid G, Tout* __restrict__ out, Tout* __restrict__ qout, const float* __restrict__ T6,
+k_read(Field<Elem> f, Grid G, Tout* __restrict__ out, Tout* __restrict__ qout,
+       const typename Storage<Elem>::real* __restrict__ T6,
        const float* __restrict__ src, const PopConsts<typename Storage<Elem>::real> k) {
   using R = typename Storage<Elem>::real;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -211,7 +212,8 @@ __device__ void sym3_inverse(const double m[6], double inv[6], double& det) {
   inv[5] = (a * d - b * b) * id;
 }
 
-__global__ void k_tensor(const float* __restrict__ in, int is_params, float* __restrict__ T6, size_t N,
+template <typename TT>
+__global__ void k_tensor(const float* __restrict__ in, int is_params, TT* __restrict__ T6, size_t N,
                          unsigned long long* bad) {
   const size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (n >= N) return;
@@ -258,7 +260,7 @@ __global__ void k_tensor(const float* __restrict__ in, int is_params, float* __r
       t6[q] = 12.0 * s;
     }
   }
-  for (int q = 0; q < 6; ++q) T6[q * N + n] = (float)t6[q];
+  for (int q = 0; q < 6; ++q) T6[q * N + n] = (TT)t6[q];
 }
 
 template <typename Elem>
@@ -292,14 +294,16 @@ template <typename Elem>
 cudaError_t read_t(const StateIO& S, void* out, void* q, int out_f32, int what, cudaStream_t s) {
   Grid G{S.nx, S.ny, S.nz, S.N, S.dirichlet};
   dim3 b = block2d(S.nx), g = grid2d(b, S.nx, S.ny, S.nz);
+  using R = typename Storage<Elem>::real;
   const auto& k = consts_of<Elem>(S);
   Field<Elem> f = field_of<Elem>(S);
+  const R* T6 = static_cast<const R*>(S.T6);
   if (out_f32) {
-    if (what == 0) k_read<Elem, float, 0><<<g, b, 0, s>>>(f, G, (float*)out, (float*)q, S.T6, S.src, k);
-    else k_read<Elem, float, 1><<<g, b, 0, s>>>(f, G, (float*)out, (float*)q, S.T6, S.src, k);
+    if (what == 0) k_read<Elem, float, 0><<<g, b, 0, s>>>(f, G, (float*)out, (float*)q, T6, S.src, k);
+    else k_read<Elem, float, 1><<<g, b, 0, s>>>(f, G, (float*)out, (float*)q, T6, S.src, k);
   } else {
-    if (what == 0) k_read<Elem, double, 0><<<g, b, 0, s>>>(f, G, (double*)out, (double*)q, S.T6, S.src, k);
-    else k_read<Elem, double, 1><<<g, b, 0, s>>>(f, G, (double*)out, (double*)q, S.T6, S.src, k);
+    if (what == 0) k_read<Elem, double, 0><<<g, b, 0, s>>>(f, G, (double*)out, (double*)q, T6, S.src, k);
+    else k_read<Elem, double, 1><<<g, b, 0, s>>>(f, G, (double*)out, (double*)q, T6, S.src, k);
   }
   return cudaGetLastError();
 }
@@ -352,11 +356,12 @@ cudaError_t launch_reduce(const StateIO& S, double* scratch, double* out4, cudaS
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_tensor_prepass(const float* in, int is_params, float* T6, size_t N, unsigned long long* bad,
-                                  cudaStream_t s) {
+cudaError_t launch_tensor_prepass(const float* in, int is_params, void* T6, int t6_f64, size_t N,
+                                  unsigned long long* bad, cudaStream_t s) {
   const int b = 256;
   const size_t g = (N + b - 1) / b;
-  k_tensor<<<(unsigned)g, b, 0, s>>>(in, is_params, T6, N, bad);
+  if (t6_f64) k_tensor<double><<<(unsigned)g, b, 0, s>>>(in, is_params, static_cast<double*>(T6), N, bad);
+  else k_tensor<float><<<(unsigned)g, b, 0, s>>>(in, is_params, static_cast<float*>(T6), N, bad);
   return cudaGetLastError();
 }
 

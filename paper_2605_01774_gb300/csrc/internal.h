@@ -19,7 +19,7 @@ struct StepLaunch {
   const float* sin;             // deviation scale plane in
   void* pout;
   float* sout;
-  const float* T6;              // per-node T = 2I - S [6][N] or null (uniform T in consts)
+  const void* T6;               // per-node T = 2I - S [6][N] (double for FP64, else float) or null
   const float* src;             // per-node source [N] or null
   unsigned long long* counters; // [0] fallback count
   const PopConsts<double>* kd;  // host copies, passed by value to the kernel
@@ -34,7 +34,7 @@ struct StateIO {
   int dirichlet;
   void* pops;                   // storage buffer (read: const)
   float* scale;
-  const float* T6;
+  const void* T6;               // double for FP64, else float
   const float* src;
   const PopConsts<double>* kd;
   const PopConsts<float>* kf;
@@ -46,8 +46,9 @@ cudaError_t launch_read_state(const StateIO& S, void* out, void* q_out, int out_
 size_t reduce_blocks(const StateIO& S);
 cudaError_t launch_reduce(const StateIO& S, double* scratch, double* out4, cudaStream_t s);
 
-// Tensor pre-pass: D6 or theta6 (float [6][N]) -> T6 (float [6][N]); bad_count counts non-SPD nodes.
-cudaError_t launch_tensor_prepass(const float* in, int is_params, float* T6, size_t N,
+// Tensor pre-pass: D6 or theta6 (float [6][N]) -> T6 ([6][N], double if t6_f64 else float);
+// bad_count counts non-SPD nodes.
+cudaError_t launch_tensor_prepass(const float* in, int is_params, void* T6, int t6_f64, size_t N,
                                   unsigned long long* bad_count, cudaStream_t s);
 
 }  // namespace elbm

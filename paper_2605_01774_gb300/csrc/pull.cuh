@@ -53,8 +53,9 @@ __device__ __forceinline__ void pull_node(R (&g)[Q], const Field<Elem>& f, const
   }
 }
 
+// Per-node T = 2I - S: stored in the arithmetic type R ([6][N]); null = uniform.
 template <typename R>
-__device__ __forceinline__ Sym6<R> load_T(const float* __restrict__ T6, size_t N, int n, const Sym6<R>& uni) {
+__device__ __forceinline__ Sym6<R> load_T(const R* __restrict__ T6, size_t N, int n, const Sym6<R>& uni) {
   if (T6 == nullptr) return uni;
   Sym6<R> t;
   t.xx = __ldg(T6 + n);

@@ -8,7 +8,8 @@ namespace elbm {
 
 template <typename Elem, int VEL>
 __global__ void __launch_bounds__(256)
-k_step(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G, const float* __restrict__ T6,
+k_step(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G,
+       const typename Storage<Elem>::real* __restrict__ T6,
        const float* __restrict__ src, int fallback, unsigned long long* __restrict__ counters,
        const PopConsts<typename Storage<Elem>::real> k) {
   using R = typename Storage<Elem>::real;
@@ -48,7 +49,8 @@ static cudaError_t launch_t(const StepLaunch& L, cudaStream_t s) {
   dim3 g((L.nx + b.x - 1) / b.x, (L.ny + b.y - 1) / b.y, L.nz);
   const PopConsts<R>& k = *reinterpret_cast<const PopConsts<R>*>(std::is_same<R, double>::value ? (const void*)L.kd
                                                                                                : (const void*)L.kf);
-  k_step<Elem, VEL><<<g, b, 0, s>>>(in, static_cast<Elem*>(L.pout), L.sout, G, L.T6, L.src, L.fallback, L.counters, k);
+  k_step<Elem, VEL><<<g, b, 0, s>>>(in, static_cast<Elem*>(L.pout), L.sout, G, static_cast<const R*>(L.T6), L.src,
+                                    L.fallback, L.counters, k);
   return cudaGetLastError();
 }
 

@@ -107,13 +107,15 @@ def gaussian(dims, mu, sigma, peak=1.0):
 def smooth_noise(dims, g: np.random.Generator, sigma: float) -> np.ndarray:
     """White noise low-passed by a periodic Gaussian filter of width sigma nodes."""
     nx, ny, nz = dims
+    sigma = min(sigma, min(dims) / 6.0)      # keep some variance on small boxes
     w = g.standard_normal((nz, ny, nx))
     kz = np.fft.fftfreq(nz)[:, None, None]
     ky = np.fft.fftfreq(ny)[None, :, None]
     kx = np.fft.fftfreq(nx)[None, None, :]
     filt = np.exp(-2.0 * (math.pi * sigma) ** 2 * (kx ** 2 + ky ** 2 + kz ** 2))
     out = np.real(np.fft.ifftn(np.fft.fftn(w) * filt))
-    return out / max(out.std(), 1e-300)
+    out -= out.mean()
+    return out / max(out.std(), 1e-12)
 
 
 def porous_mask(dims, seed: int, porosity=0.6, sigma=3.0) -> np.ndarray:
