@@ -122,12 +122,14 @@ __device__ __forceinline__ bool collide_node(R (&g)[Q], const Sym6<R>& T, const 
     for (int i = 1; i < Q; ++i) mn = mn < gs[i] ? mn : gs[i];
     if (mn < k.eps) {
       took = true;
+      // alpha = min over Omega_i < 0 of (g_i - eps) / (-Omega_i), capped at 1.  A ratio is
+      // below 1 exactly when g_i + Omega_i < eps, so only the violating populations (a few
+      // per node) need a division.
       R alpha = R(1);
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        const R om = gs[i] - g[i];
-        if (om < R(0)) {
-          const R r = (g[i] - k.eps) / (-om);
+        if (gs[i] < k.eps && g[i] > gs[i]) {
+          const R r = (g[i] - k.eps) / (g[i] - gs[i]);
           alpha = r < alpha ? r : alpha;
         }
       }

@@ -49,7 +49,8 @@ def oracle_problem(D=None, S_field_D=None, u=(0, 0, 0), bc=None, source=None, th
         S = O.relaxation_matrix(Dm)
     else:
         S = O.relaxation_matrix(torch.as_tensor(np.asarray(D)))
-    src = None if source is None else torch.as_tensor(source)
+    # the library takes the source as FP32: give the oracle the same rounded values
+    src = None if source is None else torch.as_tensor(np.asarray(source).astype(np.float32).astype(np.float64))
     return O.Problem(u=u, S=S, dirichlet_x=bc, source=src, theta=theta, eps=eps, fallback=fallback,
                      lam_mode=lam_mode)
 
