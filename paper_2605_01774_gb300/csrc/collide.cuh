@@ -11,7 +11,8 @@
 //     kappa = [sum dh_i K3_i c_i.a + phi sum dh_i L_i] / [sum dh_i^2 M_i],
 //     K3_i = 3 (1/P_i - 1), L_i = ln P_i - 3 c_i.u + 1.5 u.u, M_i = 1/(W_i P_i),
 // and kappa = 0 where u = 0 (both numerator terms vanish identically), where
-// sum dh_i^2 M_i <= theta^2 phi^2 (i.e. <dh|dh>_H <= theta^2 phi), or phi <= 0.
+// sum dh_i^2 M_i <= theta^2 phi^2 (i.e. <dh|dh>_H <= theta^2 phi), or where phi is not
+// above 1e-30 (FP32) / 1e-300 (FP64), below which the H-products are not resolvable.
 // The positivity fallback (Eq. method-alpha) shortens g* - g when some g*_i < eps.
 #pragma once
 #include "lattice.cuh"
@@ -96,19 +97,24 @@ __device__ __forceinline__ bool collide_node(R (&g)[Q], const Sym6<R>& T, const 
 #pragma unroll
     for (int i = 0; i < Q; ++i) gs[i] = phi * R(w_of(i)) + R(3.0 * w_of(i)) * ca.d[i];
   } else {
+    // kappa is a ratio of two sums that are homogeneous of degree 2 in (g, phi, j, a); it is
+    // evaluated on the phi-relative quantities dh/phi, j/phi, a/phi, where neither sum can
+    // underflow in FP32 and the guard reads sum (dh/phi)^2 M > theta^2.
     R kappa = R(0);
-    {
-      const Dots<R> cj(jx, jy, jz);
-      const Dots<R> ca(ax, ay, az);
+    const R tiny = sizeof(R) == 4 ? R(1e-30) : R(1e-300);
+    if (phi > tiny) {
+      const R inv = R(1) / phi;
+      const Dots<R> cj(jx * inv, jy * inv, jz * inv);
+      const Dots<R> ca(ax * inv, ay * inv, az * inv);
       R num = R(0), den = R(0);
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        R dh = g[i] - phi * k.E[i];
+        R dh = g[i] * inv - k.E[i];
         dh = dh - R(3.0 * w_of(i)) * cj.d[i];
-        num += dh * (k.K3[i] * ca.d[i] + phi * k.L[i]);
+        num += dh * (k.K3[i] * ca.d[i] + k.L[i]);
         den += dh * (dh * k.M[i]);
       }
-      if (phi > R(0) && den > k.theta2 * phi * phi) kappa = num / den;
+      if (den > k.theta2) kappa = num / den;
     }
     const R psi = (R(1) + kappa) * phi;
     const Dots<R> cb(ax + kappa * jx, ay + kappa * jy, az + kappa * jz);

@@ -6,8 +6,17 @@
 
 namespace elbm {
 
+// Resident blocks per SM requested from the register allocator (256 threads each).
+#ifndef ELBM_STEP_MINB
+#define ELBM_STEP_MINB 3
+#endif
+template <typename Elem>
+constexpr int step_min_blocks() {
+  return std::is_same<Elem, double>::value ? 1 : ELBM_STEP_MINB;
+}
+
 template <typename Elem, int VEL>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, step_min_blocks<Elem>())
 k_step(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G,
        const typename Storage<Elem>::real* __restrict__ T6,
        const float* __restrict__ src, int fallback, unsigned long long* __restrict__ counters,

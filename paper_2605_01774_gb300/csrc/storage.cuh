@@ -40,8 +40,8 @@ struct Storage {
 
   // Value of population i stored at node `src` (i is a constant after unrolling).
   static __device__ __forceinline__ real load(const Elem* __restrict__ pops, const float* __restrict__ scale,
-                                              size_t N, int i, int src, real E_i) {
-    const Elem v = __ldg(pops + (size_t)i * N + src);
+                                              int N, int i, int src, real E_i) {
+    const Elem v = __ldg(pops + (i * N + src));  // 27 N < 2^31 is checked at creation
     if constexpr (dev) {
       const float s = __ldg(scale + src);
       return s * fmaf(float(w_of(i)), Codec<Elem>::to_f(v), E_i);
@@ -51,7 +51,7 @@ struct Storage {
   }
 
   // Write the 27 post-collision values of node n.
-  static __device__ __forceinline__ void store(Elem* __restrict__ pops, float* __restrict__ scale, size_t N,
+  static __device__ __forceinline__ void store(Elem* __restrict__ pops, float* __restrict__ scale, int N,
                                                int n, const real (&a)[Q], const real (&E)[Q]) {
     if constexpr (dev) {
       float phi = 0.f;
@@ -65,17 +65,17 @@ struct Storage {
           const float r = fmaf(a[i], inv, -E[i]) * float(1.0 / w_of(i));
           const Elem q = Codec<Elem>::from_f(r);
           s = fmaf(float(w_of(i)), Codec<Elem>::to_f(q), s);
-          pops[(size_t)i * N + n] = q;
+          pops[i * N + n] = q;
         }
         scale[n] = phi / (1.0f + s);
       } else {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) pops[(size_t)i * N + n] = Codec<Elem>::from_f(0.f);
+        for (int i = 0; i < Q; ++i) pops[i * N + n] = Codec<Elem>::from_f(0.f);
         scale[n] = phi;
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) pops[(size_t)i * N + n] = a[i];
+      for (int i = 0; i < Q; ++i) pops[i * N + n] = a[i];
     }
   }
 };

@@ -44,10 +44,11 @@ def lib() -> C.CDLL:
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB):
-        raise ImportError(f"{LIB} is not built; run `python -m paper_2605_01774_gb300.build` "
+    path = os.environ.get("ELBM_LIBRARY", LIB)     # a custom build of the same ABI
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is not built; run `python -m paper_2605_01774_gb300.build` "
                           "(the CUDA library is required, there is no CPU path)")
-    L = C.CDLL(LIB)
+    L = C.CDLL(path)
     H, S, P, I64 = C.c_void_p, C.c_int, C.c_void_p, C.c_int64
     D = C.POINTER(C.c_double)
     sig = {
