@@ -17,6 +17,10 @@
 #pragma once
 #include "lattice.cuh"
 
+#ifndef ELBM_FB_VARIANT
+#define ELBM_FB_VARIANT 0
+#endif
+
 namespace elbm {
 
 // Per-population constants that depend on the uniform velocity (host-computed in FP64).
@@ -76,12 +80,14 @@ __device__ __forceinline__ void moments(const R (&g)[Q], R& phi, R& mx, R& my, R
 }
 
 // VEL = 0: u = 0 exactly (kappa = 0); VEL = 1: uniform u from PopConsts.
-// Returns true if the positivity fallback was taken.
+// Returns true if the positivity fallback was taken; phi_out receives the node's phi,
+// which the collision conserves exactly.
 template <typename R, int VEL>
 __device__ __forceinline__ bool collide_node(R (&g)[Q], const Sym6<R>& T, const PopConsts<R>& k,
-                                             bool fallback) {
+                                             bool fallback, R& phi_out) {
   R phi, mx, my, mz;
   moments(g, phi, mx, my, mz);
+  phi_out = phi;
   R jx = mx, jy = my, jz = mz;
   if (VEL == 1) {
     jx = mx - phi * k.ux;
@@ -132,11 +138,37 @@ __device__ __forceinline__ bool collide_node(R (&g)[Q], const Sym6<R>& T, const 
       // below 1 exactly when g_i + Omega_i < eps, so only the violating populations (a few
       // per node) need a division.
       R alpha = R(1);
+#if ELBM_FB_VARIANT == 2
+      if (sizeof(R) == 4) {
+        // branch-free: most negative (g*_i - eps)/(g_i - eps) over violating i, by cross
+        // products of phi-scaled values (no underflow), one division at the end
+        const R s = R(1) / (fabs(phi) + R(1e-30));
+        R vb = R(0), nb = R(1);
+        bool zero = false;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        if (gs[i] < k.eps && g[i] > gs[i]) {
-          const R r = (g[i] - k.eps) / (g[i] - gs[i]);
-          alpha = r < alpha ? r : alpha;
+        for (int i = 0; i < Q; ++i) {
+          const R v = (gs[i] - k.eps) * s, n = (g[i] - k.eps) * s;
+          const bool viol = gs[i] < k.eps && g[i] > gs[i];
+          zero = zero || (viol && n <= R(0));
+          const bool better = viol && v * nb < vb * n;
+          vb = better ? v : vb;
+          nb = better ? n : nb;
+        }
+        alpha = zero ? R(0) : (vb < R(0) ? nb / (nb - vb) : R(1));
+      } else
+#endif
+      {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          if (gs[i] < k.eps && g[i] > gs[i]) {
+#if ELBM_FB_VARIANT == 1
+            const R r = sizeof(R) == 4 ? R(__fdividef(float(g[i] - k.eps), float(g[i] - gs[i])))
+                                       : (g[i] - k.eps) / (g[i] - gs[i]);
+#else
+            const R r = (g[i] - k.eps) / (g[i] - gs[i]);
+#endif
+            alpha = r < alpha ? r : alpha;
+          }
         }
       }
       alpha = alpha > R(0) ? alpha : R(0);

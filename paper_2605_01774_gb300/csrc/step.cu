@@ -8,7 +8,7 @@ namespace elbm {
 
 // Resident blocks per SM requested from the register allocator (256 threads each).
 #ifndef ELBM_STEP_MINB
-#define ELBM_STEP_MINB 3
+#define ELBM_STEP_MINB 4
 #endif
 template <typename Elem>
 constexpr int step_min_blocks() {
@@ -37,8 +37,9 @@ k_step(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G
       for (int i = 0; i < Q; ++i) g[i] += r * k.E[i];
     }
     const Sym6<R> T = load_T<R>(T6, G.N, n, k.T);
-    took = collide_node<R, VEL>(g, T, k, fallback != 0);
-    Storage<Elem>::store(pout, sout, G.N, n, g, k.E);
+    R phi;
+    took = collide_node<R, VEL>(g, T, k, fallback != 0, phi);
+    Storage<Elem>::store(pout, sout, G.N, n, g, k.E, phi);
   }
   const unsigned m = __ballot_sync(0xffffffffu, took);
   if (m != 0u && ((threadIdx.y * blockDim.x + threadIdx.x) & 31) == 0) atomicAdd(counters, (unsigned long long)__popc(m));

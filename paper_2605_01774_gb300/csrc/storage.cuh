@@ -50,13 +50,17 @@ struct Storage {
     }
   }
 
-  // Write the 27 post-collision values of node n.
+  // Write the 27 post-collision values of node n.  `mass` is sum_i a_i when the caller
+  // knows it exactly (a collision conserves the node's phi); pass NaN to have it summed.
   static __device__ __forceinline__ void store(Elem* __restrict__ pops, float* __restrict__ scale, int N,
-                                               int n, const real (&a)[Q], const real (&E)[Q]) {
+                                               int n, const real (&a)[Q], const real (&E)[Q], real mass) {
     if constexpr (dev) {
-      float phi = 0.f;
+      float phi = mass;
+      if (!(phi == phi)) {
+        phi = 0.f;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) phi += a[i];
+        for (int i = 0; i < Q; ++i) phi += a[i];
+      }
       if (fabsf(phi) > 1e-30f) {
         const float inv = 1.0f / phi;
         float s = 0.f;
