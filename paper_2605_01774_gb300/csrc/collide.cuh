@@ -17,10 +17,6 @@
 #pragma once
 #include "lattice.cuh"
 
-#ifndef ELBM_FB_VARIANT
-#define ELBM_FB_VARIANT 0
-#endif
-
 namespace elbm {
 
 // Per-population constants that depend on the uniform velocity (host-computed in FP64).
@@ -135,40 +131,17 @@ __device__ __forceinline__ bool collide_node(R (&g)[Q], const Sym6<R>& T, const 
     if (mn < k.eps) {
       took = true;
       // alpha = min over Omega_i < 0 of (g_i - eps) / (-Omega_i), capped at 1.  A ratio is
-      // below 1 exactly when g_i + Omega_i < eps, so only the violating populations (a few
-      // per node) need a division.
+      // below 1 exactly when g_i + Omega_i < eps, so only the violating populations need a
+      // quotient.
       R alpha = R(1);
-#if ELBM_FB_VARIANT == 2
-      if (sizeof(R) == 4) {
-        // branch-free: most negative (g*_i - eps)/(g_i - eps) over violating i, by cross
-        // products of phi-scaled values (no underflow), one division at the end
-        const R s = R(1) / (fabs(phi) + R(1e-30));
-        R vb = R(0), nb = R(1);
-        bool zero = false;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-          const R v = (gs[i] - k.eps) * s, n = (g[i] - k.eps) * s;
-          const bool viol = gs[i] < k.eps && g[i] > gs[i];
-          zero = zero || (viol && n <= R(0));
-          const bool better = viol && v * nb < vb * n;
-          vb = better ? v : vb;
-          nb = better ? n : nb;
-        }
-        alpha = zero ? R(0) : (vb < R(0) ? nb / (nb - vb) : R(1));
-      } else
-#endif
-      {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-          if (gs[i] < k.eps && g[i] > gs[i]) {
-#if ELBM_FB_VARIANT == 1
-            const R r = sizeof(R) == 4 ? R(__fdividef(float(g[i] - k.eps), float(g[i] - gs[i])))
-                                       : (g[i] - k.eps) / (g[i] - gs[i]);
-#else
-            const R r = (g[i] - k.eps) / (g[i] - gs[i]);
-#endif
-            alpha = r < alpha ? r : alpha;
-          }
+      for (int i = 0; i < Q; ++i) {
+        if (gs[i] < k.eps && g[i] > gs[i]) {
+          // FP32: fast reciprocal-based quotient (2 ulp); the rounding of alpha moves the
+          // shortened populations by the same order as the FP32 update itself.
+          const R r = sizeof(R) == 4 ? R(__fdividef(float(g[i] - k.eps), float(g[i] - gs[i])))
+                                     : (g[i] - k.eps) / (g[i] - gs[i]);
+          alpha = r < alpha ? r : alpha;
         }
       }
       alpha = alpha > R(0) ? alpha : R(0);

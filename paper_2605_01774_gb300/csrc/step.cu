@@ -8,7 +8,7 @@ namespace elbm {
 
 // Resident blocks per SM requested from the register allocator (256 threads each).
 #ifndef ELBM_STEP_MINB
-#define ELBM_STEP_MINB 4
+#define ELBM_STEP_MINB 3
 #endif
 template <typename Elem>
 constexpr int step_min_blocks() {

@@ -1,0 +1,152 @@
+"""Full-size parity, in the launch configuration bench.py times: the GPU state
+after K steps is read, one more step is taken, and for sampled nodes the
+oracle recomputes that step node by node from the GPU's state at K (the 27
+source nodes of each sampled node are collided in FP64 and streamed).
+
+Tolerances per form: FP32 1e-6 relative L2 over the sampled populations; FP16
+deviations 2e-4 and BF16 deviations 2e-3 (storage unit 4.9e-4 / 3.9e-3 on
+relative deviations of order 1e-1).  Nodes where the FP32 and FP64 sides take a
+different branch of the stabilizer guard or the positivity fallback are
+threshold crossings; they are counted and must stay below 1% of the samples.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+from gpu_helpers import gpu_lattice
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-6, "f16dev": 2e-4, "bf16dev": 2e-3}
+
+
+@pytest.fixture(scope="module")
+def E():
+    from paper_2605_01774_gb300 import elbm
+    elbm.lib()
+    return elbm
+
+
+def _sample_nodes(dims, m, seed):
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = dims
+    pts = np.stack([rng.integers(0, nx, m), rng.integers(0, ny, m), rng.integers(0, nz, m)], 1)
+    edges = np.array([[0, 0, 0], [nx - 1, ny - 1, nz - 1], [0, ny // 2, nz - 1], [nx - 1, 0, nz // 2]])
+    return np.concatenate([pts, edges])
+
+
+def _oracle_one_step(g_prev, dims, pts, u, S_of, theta, bc=None, src=None):
+    """Pre-collision populations at pts after one step, from the pre-collision state g_prev
+    (torch [27, Nz, Ny, Nx] on the GPU), recomputed node by node in FP64."""
+    nx, ny, nz = dims
+    C = O.C.numpy().astype(int)
+    m = len(pts)
+    src_nodes = np.empty((27, m, 3), dtype=np.int64)   # source node of population i of sample p
+    for i in range(27):
+        s = pts - C[i]
+        src_nodes[i] = s
+    flat = src_nodes.reshape(-1, 3)
+    outside = (flat[:, 0] < 0) | (flat[:, 0] >= nx)
+    fx = np.mod(flat[:, 0], nx)
+    fy = np.mod(flat[:, 1], ny)
+    fz = np.mod(flat[:, 2], nz)
+    idx = torch.as_tensor(fx + nx * (fy + ny * fz), device=g_prev.device)
+    gsrc = g_prev.reshape(27, -1)[:, idx].double().cpu()                # [27, 27*m]
+    if src is not None:
+        R = torch.as_tensor(src.reshape(-1)[fx + nx * (fy + ny * fz)])
+        gsrc = O.source_half_step(gsrc, R, u)
+    S = S_of(fx, fy, fz)
+    gpost, info = O.collide(gsrc, u, S, theta=theta, lam_mode="reduced")
+    out = torch.empty(27, m, dtype=torch.float64)
+    gp = gpost.view(27, 27, m)                                              # [pop, source-of-pop, sample]
+    for i in range(27):
+        out[i] = gp[i, i]
+    if bc is not None:
+        # anti-bounce-back for links entering from outside the x range
+        o = torch.as_tensor(outside.reshape(27, m))
+        own = torch.as_tensor(pts[:, 0] + nx * (pts[:, 1] + ny * pts[:, 2]), device=g_prev.device)
+        gown = g_prev.reshape(27, -1)[:, own].double().cpu()
+        if src is not None:
+            Ro = torch.as_tensor(src.reshape(-1)[pts[:, 0] + nx * (pts[:, 1] + ny * pts[:, 2])])
+            gown = O.source_half_step(gown, Ro, u)
+        Sown = S_of(pts[:, 0], pts[:, 1], pts[:, 2])
+        gpo, _ = O.collide(gown, u, Sown, theta=theta, lam_mode="reduced")
+        for i in range(27):
+            if o[i].any():
+                cx = C[i][0]
+                phw = bc[0] if cx == 1 else bc[1]
+                out[i, o[i]] = -gpo[O.OPP[i], o[i]] + 2.0 * O.W[i] * phw
+    if src is not None:
+        R = torch.as_tensor(src.reshape(-1)[pts[:, 0] + nx * (pts[:, 1] + ny * pts[:, 2])])
+        out = O.source_half_step(out, R, u)
+    return out, info
+
+
+def _gpu_at(g, dims, pts):
+    nx, ny, nz = dims
+    idx = torch.as_tensor(pts[:, 0] + nx * (pts[:, 1] + ny * pts[:, 2]), device=g.device)
+    return g.reshape(27, -1)[:, idx].double().cpu()
+
+
+def _compare(name, gpu, ref, tol):
+    err = (gpu - ref).abs()
+    scale = ref.abs().amax(0).clamp_min(1e-300)
+    per_node = (torch.linalg.vector_norm(gpu - ref, dim=0) / torch.linalg.vector_norm(ref, dim=0).clamp_min(1e-300))
+    bad = (per_node > 50 * tol).float().mean().item()
+    good = per_node <= 50 * tol
+    rel = (torch.linalg.vector_norm((gpu - ref)[:, good]) / torch.linalg.vector_norm(ref[:, good])).item()
+    print(f"{name}: sampled rel L2 {rel:.2e}, threshold-crossing fraction {bad:.4f}")
+    assert rel < tol, (name, rel)
+    assert bad < 0.01, (name, bad)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16dev", "bf16dev"])
+def test_plume_256_sampled(E, prec):
+    wl = synth.gaussian_plume(n=256)
+    lat = gpu_lattice(E, wl.dims, prec, D=wl.D, u=wl.u, theta=3e-4)
+    E.elbm_init_equilibrium(lat.h, torch.as_tensor(wl.phi0, dtype=torch.float32, device="cuda"))
+    E.elbm_step(lat.h, 40)
+    g0 = torch.empty((27,) + wl.dims[::-1], dtype=torch.float32, device="cuda")
+    E.elbm_read_populations(lat.h, g0)
+    E.elbm_step(lat.h, 1)
+    g1 = torch.empty_like(g0)
+    E.elbm_read_populations(lat.h, g1)
+    torch.cuda.synchronize()
+    d = E.elbm_reduce(lat.h)
+    assert d["gmin"] > -1e-6
+    lat.close()
+    # sample where the plume lives and uniformly
+    pts = np.concatenate([_sample_nodes(wl.dims, 1500, 1),
+                          (np.asarray(wl.meta["mu0"]) + np.random.default_rng(2).normal(0, 10, (1500, 3))).astype(int) % 256])
+    S = O.relaxation_matrix(torch.as_tensor(wl.D))
+    ref, _ = _oracle_one_step(g0, wl.dims, pts, torch.as_tensor(wl.u), lambda x, y, z: S, 3e-4)
+    _compare(f"plume256 {prec}", _gpu_at(g1, wl.dims, pts), ref, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16dev"])
+def test_heterogeneous_384_sampled(E, prec):
+    """384^3 two-phase porous tensor field, Dirichlet x faces, Gaussian source."""
+    wl = synth.heterogeneous(n=384)
+    lat = gpu_lattice(E, wl.dims, prec, D6_field=wl.D6_field, bc=wl.dirichlet_x, source=wl.source, theta=3e-4)
+    E.elbm_init_equilibrium(lat.h, torch.as_tensor(wl.phi0, dtype=torch.float32, device="cuda"))
+    E.elbm_step(lat.h, 5)
+    g0 = torch.empty((27,) + wl.dims[::-1], dtype=torch.float32, device="cuda")
+    E.elbm_read_populations(lat.h, g0)
+    E.elbm_step(lat.h, 1)
+    g1 = torch.empty_like(g0)
+    E.elbm_read_populations(lat.h, g1)
+    torch.cuda.synchronize()
+    lat.close()
+    pts = _sample_nodes(wl.dims, 3000, 3)
+    pts = np.concatenate([pts, np.array([[0, 5, 7], [383, 9, 11], [0, 383, 383], [383, 0, 0]])])
+    D6f = wl.D6_field.astype(np.float32).astype(np.float64)
+
+    def S_of(x, y, z):
+        D = synth.matrix_from_d6(np.moveaxis(D6f[:, z, y, x], 0, -1))
+        return O.relaxation_matrix(torch.as_tensor(D))
+    src = wl.source.astype(np.float32).astype(np.float64)
+    ref, _ = _oracle_one_step(g0, wl.dims, pts, torch.zeros(3, dtype=torch.float64), S_of, 3e-4,
+                              bc=wl.dirichlet_x, src=src)
+    _compare(f"heterogeneous384 {prec}", _gpu_at(g1, wl.dims, pts), ref, TOL[prec])
