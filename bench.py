@@ -59,14 +59,17 @@ def measured_peaks():
 
 def ncu_traffic(form: str):
     """Per-launch DRAM bytes from the committed ncu summary, if it was taken on the current kernel."""
-    p = os.path.join(ROOT, "profiles", "step_traffic.json")
+    p = os.path.join(ROOT, "profiles", "step_traffic.txt")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
-    if d.get("kernel_hash") != kernel_hash():
+    vals = {}
+    for line in open(p):
+        parts = line.split()
+        if len(parts) == 2 and not line.startswith("#"):
+            vals[parts[0]] = parts[1]
+    if vals.get("kernel_hash") != kernel_hash() or form not in vals:
         return None
-    e = d.get("forms", {}).get(form)
-    return None if e is None else float(e["dram_bytes_per_launch"])
+    return float(vals[form])
 
 
 class ClockSampler:

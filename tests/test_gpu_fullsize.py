@@ -91,9 +91,12 @@ def _gpu_at(g, dims, pts):
 
 
 def _compare(name, gpu, ref, tol):
-    err = (gpu - ref).abs()
-    scale = ref.abs().amax(0).clamp_min(1e-300)
-    per_node = (torch.linalg.vector_norm(gpu - ref, dim=0) / torch.linalg.vector_norm(ref, dim=0).clamp_min(1e-300))
+    # per-node error relative to the node's own size, with an absolute floor of 1e-6 of the
+    # largest sampled node: far-tail nodes (phi down to 1e-38) are compared in absolute terms,
+    # where FP32 flush-to-zero and the phi > 1e-30 stabilizer guard legitimately differ
+    nrm = torch.linalg.vector_norm(ref, dim=0)
+    floor = 1e-6 * nrm.max()
+    per_node = torch.linalg.vector_norm(gpu - ref, dim=0) / torch.maximum(nrm, floor)
     bad = (per_node > 50 * tol).float().mean().item()
     good = per_node <= 50 * tol
     rel = (torch.linalg.vector_norm((gpu - ref)[:, good]) / torch.linalg.vector_norm(ref[:, good])).item()
