@@ -199,6 +199,39 @@ elbm_status elbm_checkpoint_load(elbm_handle h, const void* buf, size_t bytes);
  * after every step (A/B swap).  Owned by the library. */
 elbm_status elbm_state_pointers(elbm_handle h, void** pops, void** scale);
 
+/* ------------------------------------------------ allocation-free diagnostics */
+
+/* The paper has no counterpart of this call; it is a service for callers.
+ *
+ * Same diagnostics as elbm_reduce (mass, entropy, min g; out4[3] = number of
+ * non-finite populations) for a population state the caller holds, computed
+ * without allocating any device memory.  For callers that cannot allocate at
+ * that moment: a process whose device memory is fully reserved by another
+ * allocator (a framework's caching allocator, a memory pool owning the GPU), or
+ * a monitoring hook inside a time-stepping loop where an allocation that blocks
+ * or fails is not acceptable (e.g. reporting after an out-of-memory error).
+ *
+ * pops/scale: post-collision buffer in this library's storage layout for `prec`
+ * (device pointers, e.g. from elbm_state_pointers; scale only for the deviation
+ * formats, else NULL).  dims, u, bc: as given to the handle that produced the
+ * state (bc NULL = periodic).  source: the FP32 source plane on the device, or
+ * NULL.  out4: 4 doubles, host or device.  Work is ordered on cuda_stream; a
+ * host out4 synchronises it.
+ *
+ * Scratch: a fixed device array of 4096 partial sums (131 104 bytes per GPU
+ * that loads the library, held until the process exits); the kernel strides over
+ * the lattice, so every lattice the library accepts fits.  Lattices beyond the
+ * library's limit (an axis above 65535, or 27 N >= 2^31) are rejected with
+ * ELBM_ERR_ARG.  The first call on a device looks up the array's device address
+ * (once per device, with that device current); make that first call before any
+ * stream capture.  Every call reuses the same array and leaves its contents
+ * behind: calls that overlap on the GPU (other streams, other host threads on
+ * the same device) race and must be serialised by the caller.
+ * Errors: ELBM_ERR_ARG, ELBM_ERR_CUDA. */
+elbm_status elbm_reduce_noalloc(const void* pops, const float* scale, const int64_t dims[3],
+                                elbm_precision prec, const double u[3], const elbm_bc* bc,
+                                const float* source, void* cuda_stream, double out4[4]);
+
 /* ------------------------------------------------ host-only validation (no GPU) */
 
 /* ELBM_OK if D6 is SPD, else ELBM_ERR_NOT_SPD. */

@@ -74,6 +74,7 @@ def lib() -> C.CDLL:
         "elbm_checkpoint_save": (S, [H, P, C.c_size_t]),
         "elbm_checkpoint_load": (S, [H, P, C.c_size_t]),
         "elbm_state_pointers": (S, [H, C.POINTER(P), C.POINTER(P)]),
+        "elbm_reduce_noalloc": (S, [P, P, C.POINTER(C.c_int64), S, D, C.POINTER(elbm_bc), P, P, P]),
         "elbm_check_tensor": (S, [D]),
         "elbm_check_velocity": (S, [D]),
         "elbm_relaxation_complement": (S, [D, D]),
@@ -232,6 +233,21 @@ def elbm_state_pointers(h):
     p, s = C.c_void_p(), C.c_void_p()
     _check(lib().elbm_state_pointers(h, C.byref(p), C.byref(s)), h)
     return p.value, s.value
+
+
+def elbm_reduce_noalloc(pops_ptr, scale_ptr, dims, prec, u, bc=None, source=None, stream=None, out=None):
+    """Diagnostics of a caller-held state without device allocation (see include/elbm.h).
+
+    pops_ptr / scale_ptr are raw device addresses (ints); out is a host numpy array of
+    4 float64 (created if None) or a device tensor.  Returns out."""
+    d = (C.c_int64 * 3)(*[int(v) for v in dims])
+    p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    b = C.byref(elbm_bc(1, float(bc[0]), float(bc[1]))) if bc is not None else None
+    if out is None:
+        out = np.zeros(4, dtype=np.float64)
+    _check(lib().elbm_reduce_noalloc(C.c_void_p(pops_ptr), C.c_void_p(scale_ptr or 0), d, p, _d(u, 3), b,
+                                     _ptr(source), _stream_ptr(stream), _ptr(out)))
+    return out
 
 
 def elbm_check_tensor(D6) -> int:
