@@ -79,6 +79,22 @@ def lib() -> C.CDLL:
         "elbm_check_velocity": (S, [D]),
         "elbm_relaxation_complement": (S, [D, D]),
     }
+    I32, PI32, PI64 = C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64)
+    sig.update({
+        "elbm_batch_create": (S, [I32, P, P, P, C.POINTER(H)]),
+        "elbm_batch_destroy": (None, [H]),
+        "elbm_batch_last_error": (C.c_char_p, [H]),
+        "elbm_batch_info": (S, [H, PI64, PI32, PI32, PI32]),
+        "elbm_batch_set_params": (S, [H, C.c_double, I32]),
+        "elbm_batch_set_wait_limit": (S, [H, I64, I32]),
+        "elbm_batch_init_equilibrium": (S, [H, P]),
+        "elbm_batch_step": (S, [H, I64, I32]),
+        "elbm_batch_synchronize": (S, [H]),
+        "elbm_batch_autotune": (S, [H, I32, PI32, PI32]),
+        "elbm_batch_read_phi": (S, [H, P]),
+        "elbm_batch_read_populations": (S, [H, I32, P]),
+        "elbm_batch_fallback_count": (S, [H, PI64]),
+    })
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
         fn.restype = res
@@ -262,6 +278,72 @@ def elbm_relaxation_complement(D6):
     out = (C.c_double * 6)()
     _check(lib().elbm_relaxation_complement(_d(D6, 6), out))
     return np.array(list(out))
+
+
+# ------------------------------------------------------------- batched domains
+def _bcheck(status, h):
+    if status != 0:
+        raise ElbmError(status, lib().elbm_batch_last_error(h).decode() if h else "")
+
+
+def elbm_batch_create(edges, D6, stream=None):
+    edges = np.ascontiguousarray(edges, dtype=np.int32)
+    D6 = np.ascontiguousarray(D6, dtype=np.float64).reshape(len(edges), 6)
+    h = C.c_void_p()
+    _check(lib().elbm_batch_create(len(edges), _ptr(edges), _ptr(D6), _stream_ptr(stream), C.byref(h)))
+    return h
+
+
+def elbm_batch_destroy(h):
+    lib().elbm_batch_destroy(h)
+
+
+def elbm_batch_info(h):
+    n, t, b, g = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32()
+    _bcheck(lib().elbm_batch_info(h, C.byref(n), C.byref(t), C.byref(b), C.byref(g)), h)
+    return dict(total_nodes=n.value, tile=t.value, blocks_per_sm=b.value, persistent_in_graph=g.value)
+
+
+def elbm_batch_set_params(h, eps=0.0, fallback=True):
+    _bcheck(lib().elbm_batch_set_params(h, float(eps), int(bool(fallback))), h)
+
+
+def elbm_batch_set_wait_limit(h, cycles, extra_arrivals=0):
+    _bcheck(lib().elbm_batch_set_wait_limit(h, int(cycles), int(extra_arrivals)), h)
+
+
+def elbm_batch_init_equilibrium(h, phi0):
+    _bcheck(lib().elbm_batch_init_equilibrium(h, _ptr(phi0)), h)
+
+
+def elbm_batch_step(h, nsteps, mode=0):
+    _bcheck(lib().elbm_batch_step(h, int(nsteps), int(mode)), h)
+
+
+def elbm_batch_synchronize(h):
+    _bcheck(lib().elbm_batch_synchronize(h), h)
+
+
+def elbm_batch_autotune(h, steps_per_trial=3):
+    t, b = C.c_int32(), C.c_int32()
+    _bcheck(lib().elbm_batch_autotune(h, int(steps_per_trial), C.byref(t), C.byref(b)), h)
+    return t.value, b.value
+
+
+def elbm_batch_read_phi(h, out):
+    _bcheck(lib().elbm_batch_read_phi(h, _ptr(out)), h)
+    return out
+
+
+def elbm_batch_read_populations(h, domain, out):
+    _bcheck(lib().elbm_batch_read_populations(h, int(domain), _ptr(out)), h)
+    return out
+
+
+def elbm_batch_fallback_count(h):
+    v = C.c_int64()
+    _bcheck(lib().elbm_batch_fallback_count(h, C.byref(v)), h)
+    return v.value
 
 
 # ------------------------------------------------------------ convenience
