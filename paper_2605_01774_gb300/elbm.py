@@ -95,6 +95,14 @@ def lib() -> C.CDLL:
         "elbm_batch_read_populations": (S, [H, I32, P]),
         "elbm_batch_fallback_count": (S, [H, PI64]),
     })
+    sig.update({
+        "elbm_adjoint_create": (S, [C.POINTER(C.c_int64), S, P, C.POINTER(H)]),
+        "elbm_adjoint_destroy": (None, [H]),
+        "elbm_adjoint_last_error": (C.c_char_p, [H]),
+        "elbm_adjoint_configure": (S, [H, D, C.c_double, I32]),
+        "elbm_adjoint_misfit": (S, [H, P, P, I64, I32, PI64, P, D, P, PI64]),
+        "elbm_adjoint_step": (S, [H, P, P, P, P, P, P]),
+    })
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
         fn.restype = res
@@ -344,6 +352,67 @@ def elbm_batch_fallback_count(h):
     v = C.c_int64()
     _bcheck(lib().elbm_batch_fallback_count(h, C.byref(v)), h)
     return v.value
+
+
+# ------------------------------------------------------------------- adjoint
+def _acheck(status, h):
+    if status != 0:
+        raise ElbmError(status, lib().elbm_adjoint_last_error(h).decode() if h else "")
+
+
+def elbm_adjoint_create(dims, prec="f64", stream=None):
+    d = (C.c_int64 * 3)(*[int(v) for v in dims])
+    p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    h = C.c_void_p()
+    _check(lib().elbm_adjoint_create(d, p, _stream_ptr(stream), C.byref(h)))
+    return h
+
+
+def elbm_adjoint_destroy(h):
+    lib().elbm_adjoint_destroy(h)
+
+
+def elbm_adjoint_configure(h, u, theta=1e-8, checkpoint_every=50):
+    _acheck(lib().elbm_adjoint_configure(h, _d(u, 3), float(theta), int(checkpoint_every)), h)
+
+
+def elbm_adjoint_misfit(h, theta6, phi0, nsteps, obs_steps, targets, grad6=None):
+    """Returns (J, n_fallback); fills grad6 (device tensor) when given."""
+    obs = np.ascontiguousarray(obs_steps, dtype=np.int64)
+    J = C.c_double()
+    nfb = C.c_int64()
+    _acheck(lib().elbm_adjoint_misfit(h, _ptr(theta6), _ptr(phi0), int(nsteps), len(obs),
+                                      obs.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(targets), C.byref(J),
+                                      _ptr(grad6), C.byref(nfb)), h)
+    return J.value, nfb.value
+
+
+def elbm_adjoint_step(h, theta6, g, gbar_next=None, g_next=None, gbar=None, grad6=None):
+    _acheck(lib().elbm_adjoint_step(h, _ptr(theta6), _ptr(g), _ptr(gbar_next), _ptr(g_next), _ptr(gbar),
+                                    _ptr(grad6)), h)
+
+
+def tensor_misfit_function():
+    """torch.autograd.Function whose forward is J(theta) and whose backward is the
+    hand-written adjoint (both computed by one elbm_adjoint_misfit call)."""
+    import torch
+
+    class TensorMisfit(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, theta, handle, phi0, nsteps, obs_steps, targets):
+            grad = torch.empty_like(theta)
+            J, nfb = elbm_adjoint_misfit(handle, theta.detach().contiguous(), phi0, nsteps, obs_steps, targets,
+                                         grad6=grad)
+            ctx.save_for_backward(grad)
+            ctx.n_fallback = nfb
+            return torch.tensor(J, dtype=torch.float64, device=theta.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            (grad,) = ctx.saved_tensors
+            return gJ.to(grad.dtype) * grad, None, None, None, None, None
+
+    return TensorMisfit
 
 
 # ------------------------------------------------------------ convenience
