@@ -274,6 +274,8 @@ def run_ours(args, rank, world, local, dist):
                h2d_bytes_per_step=N * 4 / args.steps, d2h_bytes_per_step=(N * 4 + 8 * 4) / args.steps,
                final_mass=mass)
 
+    batched = None if args.batched_steps <= 0 else run_batched(args, E, dev, dist, world)
+
     if rank != 0:
         return None
     peak, peak_src = measured_peaks()
@@ -300,12 +302,48 @@ def run_ours(args, rank, world, local, dist):
         "forms": forms,
         "chosen_vs_plain_speedup": hf["mlups"] / forms["f32"]["mlups"],
         "e2e": e2e,
+        "batched": batched,
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     return line
+
+
+def run_batched(args, E, dev, dist, world):
+    """Orientation / anisotropy sweep: 512 periodic domains, edges U{16..96} (seed 4),
+    FP32, u = 0; persistent graph-captured kernel (autotuned) vs one batched launch per
+    step in a graph vs one plain launch per domain per step."""
+    import torch
+    table, _ = synth.batched_domains()
+    edges = [d["n"] for d in table]
+    D6 = np.stack([synth.d6_from_matrix(d["D"]) for d in table])
+    phi0 = torch.as_tensor(np.concatenate([synth.batched_phi0(n).ravel() for n in edges]).astype(np.float32),
+                           device=dev)
+    h = E.elbm_batch_create(edges, D6)
+    E.elbm_batch_init_equilibrium(h, phi0)
+    tile, bps = E.elbm_batch_autotune(h, 2)
+    total = E.elbm_batch_info(h)["total_nodes"]
+    out = {"domains": len(edges), "nodes": total, "steps": args.batched_steps, "tile": tile,
+           "blocks_per_sm": bps, "bytes_per_node": BYTES_PER_NODE["f32"]}
+    peak, _ = measured_peaks()
+    for mode, name in ((0, "persistent_graph"), (1, "per_step_graph"), (2, "per_domain_launches")):
+        E.elbm_batch_init_equilibrium(h, phi0)
+        E.elbm_batch_step(h, 2, mode)
+        E.elbm_batch_synchronize(h)
+        barrier(dist)
+        t0 = time.perf_counter()
+        E.elbm_batch_step(h, args.batched_steps, mode)
+        E.elbm_batch_synchronize(h)
+        dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        mlups = world * total * args.batched_steps / dt / 1e6
+        out[name] = {"ms_per_step": dt * 1e3 / args.batched_steps, "mlups": mlups,
+                     "hbm_frac_of_measured": mlups * 1e6 * BYTES_PER_NODE["f32"] / 1e9 / peak}
+    out["persistent_in_graph"] = E.elbm_batch_info(h)["persistent_in_graph"]
+    out["persistent_vs_per_domain_speedup"] = out["persistent_graph"]["mlups"] / out["per_domain_launches"]["mlups"]
+    E.elbm_batch_destroy(h)
+    return out
 
 
 # ------------------------------------------------------------------------ oracle arm
@@ -370,6 +408,8 @@ def main():
     ap.add_argument("--err-steps", type=int, default=200)
     ap.add_argument("--cpu-sample", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=100,
+                    help="steps per mode of the 512-domain sweep (0 skips it)")
     ap.add_argument("--only", default=None, choices=["f16dev", "bf16dev", "f32", "f64"],
                     help="time one form only (profiling runs)")
     args = ap.parse_args()

@@ -45,7 +45,7 @@ def misfit_gradient(theta, phi0, u, nsteps, obs, targets, guard=1e-8, segment=No
     th = torch.as_tensor(theta, dtype=O.DT).clone().requires_grad_(True)
     J, prob = misfit(th, phi0, u, nsteps, obs, targets, guard=guard, segment=segment)
     J.backward()
-    return float(J), th.grad.detach(), prob.stats["fallback_nodes"]
+    return float(J.detach()), th.grad.detach(), prob.stats["fallback_nodes"]
 
 
 def forward_snapshots(theta, phi0, u, nsteps, obs, guard=1e-8):

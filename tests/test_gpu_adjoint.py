@@ -132,11 +132,15 @@ def test_config5_gradient_vs_central_differences(E):
     grad = torch.empty_like(th0)
     J0, nfb = E.elbm_adjoint_misfit(h, th0, phi0, 500, [250, 500], tg, grad6=grad)
     assert nfb == 0 and J0 > 0
+    # 20 seeded (node, component) pairs where the misfit is sensitive: nodes within 8 of the
+    # plume centre (far nodes have gradients of 1e-13, below the FD noise floor of ~1e-10)
     rng = np.random.default_rng(55)
-    hstep = 1e-6
+    hstep = 1e-5
     worst = 0.0
     for _ in range(20):
-        comp, node = int(rng.integers(0, 6)), int(rng.integers(0, N))
+        comp = int(rng.integers(0, 6))
+        x, y, z = (31.5 + rng.uniform(-8, 8, 3)).astype(int)
+        node = int(x + n * (y + n * z))
         tp = th0.clone()
         tp.view(6, -1)[comp, node] += hstep
         tm = th0.clone()
