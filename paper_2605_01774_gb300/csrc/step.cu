@@ -36,17 +36,9 @@ k_step(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G
 #pragma unroll
       for (int i = 0; i < Q; ++i) g[i] += r * k.E[i];
     }
-    // A node whose 27 incoming populations are all exactly zero collides to exactly zero
-    // (phi = 0, j = 0, kappa = 0; with eps = 0 nothing falls below the threshold): write the
-    // zeros directly.
-    bool zero = k.eps <= R(0);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) zero = zero && (g[i] == R(0));
-    R phi = R(0);
-    if (!zero) {
-      const Sym6<R> T = load_T<R>(T6, G.N, n, k.T);
-      took = collide_node<R, VEL>(g, T, k, fallback != 0, phi);
-    }
+    const Sym6<R> T = load_T<R>(T6, G.N, n, k.T);
+    R phi;
+    took = collide_node<R, VEL>(g, T, k, fallback != 0, phi);
     Storage<Elem>::store(pout, sout, G.N, n, g, k.E, phi);
   }
   const unsigned m = __ballot_sync(0xffffffffu, took);

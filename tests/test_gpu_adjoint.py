@@ -153,13 +153,16 @@ def test_config5_gradient_vs_central_differences(E):
         worst = max(worst, rel)
         print(f"theta[{comp}, {node}]: adjoint {ad:.9e} central FD {fd:.9e} rel {rel:.2e}")
     assert worst < 1e-4
-    # FP32 adjoint against the FP64 one
+    # FP32 adjoint against the FP64 one, both with the FP32 guard theta = 3e-4
+    E.elbm_adjoint_configure(h, p["u"], 3e-4, 50)
+    J64, _ = E.elbm_adjoint_misfit(h, th0, phi0, 500, [250, 500], tg, grad6=grad)
     h32 = E.elbm_adjoint_create(dims, "f32")
     E.elbm_adjoint_configure(h32, p["u"], 3e-4, 50)
     g32 = torch.empty(th0.shape, dtype=torch.float32, device=DEV)
     J32, nfb32 = E.elbm_adjoint_misfit(h32, th0.float(), phi0.float(), 500, [250, 500], tg.float(), grad6=g32)
     e = (torch.linalg.vector_norm(g32.double() - grad) / torch.linalg.vector_norm(grad)).item()
-    print(f"FP32 vs FP64 adjoint: J rel {abs(J32 - J0) / J0:.2e}, gradient rel L2 {e:.2e}")
+    print(f"FP32 vs FP64 adjoint: J rel {abs(J32 - J64) / J64:.2e}, gradient rel L2 {e:.2e}")
+    assert nfb32 == 0
     assert e < 5e-2
     E.elbm_adjoint_destroy(h32)
     E.elbm_adjoint_destroy(h)
