@@ -26,8 +26,6 @@ struct StepLaunch {
   const PopConsts<float>* kf;
 };
 cudaError_t launch_step(const StepLaunch& L, cudaStream_t s);
-// deviation storages (prec 2, 3): phi-relative kernel with a shared-memory scale tile
-cudaError_t launch_step_dev(const StepLaunch& L, cudaStream_t s);
 
 // State transfer.  mode 0: populations [27][N] <-> caller; mode 1: phi0 [N] -> equilibrium.
 struct StateIO {

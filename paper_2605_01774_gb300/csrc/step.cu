@@ -7,9 +7,6 @@
 namespace elbm {
 
 // Resident blocks per SM requested from the register allocator (256 threads each).
-#ifndef ELBM_DEV_KERNEL
-#define ELBM_DEV_KERNEL 1
-#endif
 #ifndef ELBM_STEP_MINB
 #define ELBM_STEP_MINB 3
 #endif
@@ -72,13 +69,8 @@ cudaError_t launch_step(const StepLaunch& L, cudaStream_t s) {
   switch (L.prec) {
     case 0: return v ? launch_t<double, 1>(L, s) : launch_t<double, 0>(L, s);
     case 1: return v ? launch_t<float, 1>(L, s) : launch_t<float, 0>(L, s);
-#if ELBM_DEV_KERNEL
-    case 2:
-    case 3: return launch_step_dev(L, s);
-#else
     case 2: return v ? launch_t<__half, 1>(L, s) : launch_t<__half, 0>(L, s);
     case 3: return v ? launch_t<__nv_bfloat16, 1>(L, s) : launch_t<__nv_bfloat16, 0>(L, s);
-#endif
   }
   return cudaErrorInvalidValue;
 }
