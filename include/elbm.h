@@ -146,6 +146,19 @@ elbm_status elbm_set_velocity_uniform(elbm_handle h, const double u[3]);
  * half-steps between consecutive steps are merged into one full step. */
 elbm_status elbm_set_source(elbm_handle h, const float* R);
 
+/* Amplitude a of the source for time-dependent sources R(x, t) = a(t) R(x) (Section
+ * 3.3 evaluates R at the mid-step time t_{n+1/2} for both half-steps of step n).  Sets the
+ * amplitude of the half-step the stored state is considered to include; must be called
+ * before elbm_init_* (ELBM_ERR_STATE otherwise).  Default 1. */
+elbm_status elbm_set_source_amplitude(elbm_handle h, double a);
+
+/* Advance nsteps steps with source amplitudes amp[0..nsteps-1] (host), amp[k] = a(t_{n+1/2})
+ * of step n = current step + k.  Step n adds (a_{n-1} + a_n)/2 R E_i to the pulled
+ * populations (trailing half of step n-1 merged with the leading half of step n); reads
+ * and writes of the state then include a_{n-1}/2 R E_i.  With a constant amplitude this
+ * is elbm_step. */
+elbm_status elbm_step_source_schedule(elbm_handle h, const double* amp, int64_t nsteps);
+
 /* --------------------------------------------------------------- state */
 
 /* Initial state g = g_eq(phi0, u) (initial populations are not stated in the

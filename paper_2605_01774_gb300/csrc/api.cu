@@ -34,6 +34,7 @@ struct elbm_ctx {
   double* d_out4 = nullptr;
   int64_t step = 0;
   bool initialized = false;
+  double src_amp = 1.0;      // source amplitude of the most recent half-step a_{n-1}
   std::string err;
 };
 
@@ -128,6 +129,8 @@ void rebuild_consts(elbm_ctx* h) {
   k.eps = h->params.eps;
   k.phi_lo = h->bc.phi_lo;
   k.phi_hi = h->bc.phi_hi;
+  k.src_step = h->src_amp;
+  k.src_half = 0.5 * h->src_amp;
   double T[6] = {0, 0, 0, 0, 0, 0};
   if (h->have_tensor && !h->tensor_field) complement6(h->D6, T);
   k.T = Sym6<double>{T[0], T[1], T[2], T[3], T[4], T[5]};
@@ -145,6 +148,8 @@ void rebuild_consts(elbm_ctx* h) {
   f.eps = (float)k.eps;
   f.phi_lo = (float)k.phi_lo;
   f.phi_hi = (float)k.phi_hi;
+  f.src_step = (float)k.src_step;
+  f.src_half = (float)k.src_half;
   f.T = Sym6<float>{(float)T[0], (float)T[1], (float)T[2], (float)T[3], (float)T[4], (float)T[5]};
 }
 
@@ -429,6 +434,34 @@ elbm_status elbm_step(elbm_handle h, int64_t nsteps) {
     h->cur = 1 - h->cur;
     h->step += 1;
   }
+  return ELBM_OK;
+}
+
+elbm_status elbm_set_source_amplitude(elbm_handle h, double a) {
+  if (!h || !std::isfinite(a)) return fail(h, ELBM_ERR_ARG, "bad amplitude");
+  if (h->initialized) return fail(h, ELBM_ERR_STATE, "the amplitude must be set before the state is initialised");
+  h->src_amp = a;
+  rebuild_consts(h);
+  return ELBM_OK;
+}
+
+elbm_status elbm_step_source_schedule(elbm_handle h, const double* amp, int64_t nsteps) {
+  if (!h || (nsteps > 0 && !amp)) return fail(h, ELBM_ERR_ARG, "null argument");
+  if (nsteps < 0) return fail(h, ELBM_ERR_ARG, "nsteps < 0");
+  for (int64_t s = 0; s < nsteps; ++s) {
+    if (!std::isfinite(amp[s])) return fail(h, ELBM_ERR_ARG, "non-finite amplitude");
+    const double a_prev = h->src_amp;
+    // this step applies the trailing half of the previous step and the leading half of this one
+    h->kd.src_step = 0.5 * (a_prev + amp[s]);
+    h->kf.src_step = (float)h->kd.src_step;
+    elbm_status st = elbm_step(h, 1);
+    h->src_amp = amp[s];
+    if (st != ELBM_OK) {
+      rebuild_consts(h);
+      return st;
+    }
+  }
+  rebuild_consts(h);
   return ELBM_OK;
 }
 

@@ -49,12 +49,12 @@ k_write(Elem* __restrict__ pops, float* __restrict__ scale, Grid G, const void* 
     const int d = dx + G.nx * (dy + G.ny * dz);
     if (!outside) {
       R v = FROM_PHI ? R(ld_in<Tin>(in, d)) * k.E[i] : R(ld_in<Tin>(in, (size_t)i * G.N + d));
-      if (src != nullptr) v -= R(0.5) * R(src[d]) * k.E[i];
+      if (src != nullptr) v -= k.src_half * R(src[d]) * k.E[i];
       a[i] = v;
     } else {
       const int o = opp_of(i);
       R v = FROM_PHI ? R(ld_in<Tin>(in, n)) * k.E[o] : R(ld_in<Tin>(in, (size_t)o * G.N + n));
-      if (src != nullptr) v -= R(0.5) * R(src[n]) * k.E[o];
+      if (src != nullptr) v -= k.src_half * R(src[n]) * k.E[o];
       const R phw = through_hi ? k.phi_hi : k.phi_lo;
       a[i] = R(2.0 * w_of(i)) * phw - v;
     }
@@ -77,7 +77,7 @@ k_read(Field<Elem> f, Grid G, Tout* __restrict__ out, Tout* __restrict__ qout,
   R g[Q];
   pull_node<Elem, R>(g, f, G, x, y, z, k);
   if (src != nullptr) {
-    const R r = R(0.5) * R(src[n]);
+    const R r = k.src_half * R(src[n]);
 #pragma unroll
     for (int i = 0; i < Q; ++i) g[i] += r * k.E[i];
   }
@@ -117,7 +117,7 @@ k_reduce_partials(Field<Elem> f, Grid G, const float* __restrict__ src, double* 
     const int n = x + G.nx * (y + G.ny * z);
     R g[Q];
     pull_node<Elem, R>(g, f, G, x, y, z, k);
-    const double r = src != nullptr ? 0.5 * (double)src[n] : 0.0;
+    const double r = src != nullptr ? (double)k.src_half * (double)src[n] : 0.0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const double v = (double)g[i] + r * (double)k.E[i];

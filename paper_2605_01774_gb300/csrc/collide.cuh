@@ -31,6 +31,8 @@ struct PopConsts {
   R eps;
   R phi_lo, phi_hi;  // Dirichlet wall values
   Sym6<R> T;         // uniform T = 2I - S
+  R src_step;        // source multiplier of this step: (a_{n-1} + a_n)/2 (merged Strang halves)
+  R src_half;        // half-step multiplier of the stored state: a_{n-1}/2
 };
 
 // c_i . v for all 27 velocities from 9 (cy, cz) partial sums.

@@ -32,7 +32,7 @@ k_step(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G
     pull_node<Elem, R>(g, in, G, x, y, z, k);
     if (src != nullptr) {
       // merged Strang half-steps of consecutive steps (Section 3.3)
-      const R r = __ldg(src + n);
+      const R r = k.src_step * R(__ldg(src + n));
 #pragma unroll
       for (int i = 0; i < Q; ++i) g[i] += r * k.E[i];
     }

@@ -62,6 +62,8 @@ def lib() -> C.CDLL:
         "elbm_set_tensor_params_field": (S, [H, P]),
         "elbm_set_velocity_uniform": (S, [H, D]),
         "elbm_set_source": (S, [H, P]),
+        "elbm_set_source_amplitude": (S, [H, C.c_double]),
+        "elbm_step_source_schedule": (S, [H, D, I64]),
         "elbm_init_equilibrium": (S, [H, P, S]),
         "elbm_write_populations": (S, [H, P, S]),
         "elbm_read_populations": (S, [H, P, S]),
@@ -194,6 +196,15 @@ def elbm_set_velocity_uniform(h, u):
 
 def elbm_set_source(h, R):
     _check(lib().elbm_set_source(h, _ptr(R)), h)
+
+
+def elbm_set_source_amplitude(h, a):
+    _check(lib().elbm_set_source_amplitude(h, float(a)), h)
+
+
+def elbm_step_source_schedule(h, amplitudes):
+    a = np.ascontiguousarray(amplitudes, dtype=np.float64)
+    _check(lib().elbm_step_source_schedule(h, a.ctypes.data_as(C.POINTER(C.c_double)), len(a)), h)
 
 
 def elbm_init_equilibrium(h, phi0):
