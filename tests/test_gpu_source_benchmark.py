@@ -47,7 +47,8 @@ def _run(E, prec, d, theta, n=128, shift=2.0):
     expected = p["S"].sum() + p["f"].astype(np.float32).astype(np.float64).sum() * p["amp"].sum()
     return dict(gre=float(np.linalg.norm(num - ex) / np.linalg.norm(ex)),
                 l2=float(np.sqrt(((num - ex) ** 2).mean())), linf=float(np.abs(num - ex).max()),
-                mass=float(num.sum() - expected), fallback=d["n_fallback"])
+                # physical mass on [0,1)^3: integral of phi = sum(phi) dx^3
+                mass=float((num.sum() - expected) / n ** 3), fallback=d["n_fallback"])
 
 
 @pytest.mark.parametrize("case", [0, 3])
