@@ -114,6 +114,17 @@ const char* elbm_status_string(elbm_status s);
 /* Set theta, eps, fallback (see elbm_params).  ELBM_ERR_ARG if theta < 0. */
 elbm_status elbm_set_params(elbm_handle h, const elbm_params* p);
 
+/* How the entropic amplitude lambda is obtained where the ghost content is above the
+ * guard.  mode 0 (default): the closed form of Eqs. (method-lambda, method-correction),
+ * which the paper uses in all its runs.  mode 1: the exact root of the entropy-
+ * stationarity condition, Eq. (method-entropy-root), sum_i dh_i ln((g_eq_i + ds_post_i +
+ * (1 - lambda) dh_i)/W_i) = 0, solved per node by safeguarded Newton in FP64 (for every
+ * precision) from the closed-form value inside the bracket where all arguments are
+ * positive; the closed form is kept where that bracket is empty.  Mode 1 is costly (27
+ * FP64 logarithms per Newton iteration) and applies only where u != 0.
+ * ELBM_ERR_ARG for other modes. */
+elbm_status elbm_set_lambda_mode(elbm_handle h, int32_t mode);
+
 /* --------------------------------------------------------- problem data */
 
 /* Uniform tensor D, 6 doubles (Dxx, Dxy, Dxz, Dyy, Dyz, Dzz), host memory.

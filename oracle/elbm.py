@@ -173,6 +173,41 @@ def entropic_amplitude(phi, g_eq, dh, ds_post, u, theta=1e-8, mode="literal"):
     return lam
 
 
+def entropy_root(g_eq, dh, ds_post, lam0):
+    """Exact root of Eq. (method-entropy-root) at each node where lam0 is not exactly 1:
+    sum_i dh_i ln((g_eq_i + ds_post_i + (1 - lam) dh_i) / W_i) = 0, by scipy's brentq on
+    the open bracket where every argument is positive (the function decreases from +inf to
+    -inf across it).  Nodes whose bracket is empty keep lam0.  (parity: the GPU's FP64
+    Newton solves the same equation.)"""
+    import numpy as np
+    from scipy.optimize import brentq
+    ge = g_eq.reshape(27, -1).double().numpy()
+    dh_ = dh.reshape(27, -1).double().numpy()
+    dp = ds_post.reshape(27, -1).double().numpy()
+    l0 = lam0.reshape(-1).double().numpy().copy()
+    w = W.numpy()
+    out = l0.copy()
+    for n in range(l0.size):
+        if l0[n] == 1.0:
+            continue
+        b = ge[:, n] + dp[:, n]
+        d = dh_[:, n]
+        pos, neg = d > 0, d < 0
+        if np.any(~pos & ~neg & ~(b > 0)) or not pos.any() or not neg.any():
+            continue
+        hi = np.min(1.0 + b[pos] / d[pos])
+        lo = np.max(1.0 + b[neg] / d[neg])
+        if not lo < hi:
+            continue
+        f = lambda lam: float(np.sum(d * np.log((b + (1.0 - lam) * d) / w)))
+        span = hi - lo
+        a_, b_ = lo + 1e-13 * span, hi - 1e-13 * span
+        if not (f(a_) > 0 > f(b_)):
+            continue
+        out[n] = brentq(f, a_, b_, xtol=1e-15, rtol=1e-15, maxiter=500)
+    return torch.as_tensor(out, dtype=DT).reshape(lam0.shape)
+
+
 def positivity_fallback(g: torch.Tensor, omega: torch.Tensor, eps: float = 0.0):
     """alpha of Eq. (method-alpha) under reading R4.  Returns (alpha, triggered)."""
     need = ((g + omega) < eps).any(0)
@@ -207,7 +242,10 @@ def collide(g: torch.Tensor, u: torch.Tensor, S: torch.Tensor, theta: float = 1e
     Sj = apply_matrix(S, j)                          # step 3, Eq. method-flux-relaxation
     omega_s = -lift(Sj)
     ds_post = ds + omega_s                           # = P((I - S) j)
-    lam = entropic_amplitude(phi, g_eq, dh, ds_post, u, theta, lam_mode)   # step 4
+    lam = entropic_amplitude(phi, g_eq, dh, ds_post, u, theta,
+                             "literal" if lam_mode == "root" else lam_mode)          # step 4
+    if lam_mode == "root":
+        lam = entropy_root(g_eq, dh, ds_post, lam)       # Eq. method-entropy-root, exactly
     omega = omega_s - lam.unsqueeze(0) * dh          # step 5, Eq. method-collision
     if fallback:
         alpha, need = positivity_fallback(g, omega, eps)   # Eq. method-alpha

@@ -35,6 +35,7 @@ struct elbm_ctx {
   int64_t step = 0;
   bool initialized = false;
   double src_amp = 1.0;      // source amplitude of the most recent half-step a_{n-1}
+  int lambda_mode = 0;       // 0 closed form, 1 exact root
   std::string err;
 };
 
@@ -131,6 +132,7 @@ void rebuild_consts(elbm_ctx* h) {
   k.phi_hi = h->bc.phi_hi;
   k.src_step = h->src_amp;
   k.src_half = 0.5 * h->src_amp;
+  k.root = h->lambda_mode;
   double T[6] = {0, 0, 0, 0, 0, 0};
   if (h->have_tensor && !h->tensor_field) complement6(h->D6, T);
   k.T = Sym6<double>{T[0], T[1], T[2], T[3], T[4], T[5]};
@@ -150,6 +152,7 @@ void rebuild_consts(elbm_ctx* h) {
   f.phi_hi = (float)k.phi_hi;
   f.src_step = (float)k.src_step;
   f.src_half = (float)k.src_half;
+  f.root = k.root;
   f.T = Sym6<float>{(float)T[0], (float)T[1], (float)T[2], (float)T[3], (float)T[4], (float)T[5]};
 }
 
@@ -434,6 +437,13 @@ elbm_status elbm_step(elbm_handle h, int64_t nsteps) {
     h->cur = 1 - h->cur;
     h->step += 1;
   }
+  return ELBM_OK;
+}
+
+elbm_status elbm_set_lambda_mode(elbm_handle h, int32_t mode) {
+  if (!h || (mode != 0 && mode != 1)) return fail(h, ELBM_ERR_ARG, "mode must be 0 or 1");
+  h->lambda_mode = mode;
+  rebuild_consts(h);
   return ELBM_OK;
 }
 

@@ -33,7 +33,42 @@ struct PopConsts {
   Sym6<R> T;         // uniform T = 2I - S
   R src_step;        // source multiplier of this step: (a_{n-1} + a_n)/2 (merged Strang halves)
   R src_half;        // half-step multiplier of the stored state: a_{n-1}/2
+  int root;          // 1: lambda from the exact entropy-stationarity root (FP64 Newton)
 };
+
+// Exact root of Eq. (method-entropy-root):
+//   f(lam) = sum_i dh_i ln((g_eq_i + ds_post_i + (1 - lam) dh_i) / W_i) = 0,
+// f decreasing (f' = -sum dh_i^2 / A_i), arguments A_i > 0 on an open bracket.  Safeguarded
+// Newton in FP64 from the closed-form lam0; returns lam0 if the bracket is empty.
+__device__ __forceinline__ double entropy_root(const double (&geq)[Q], const double (&dsp)[Q], const double (&dh)[Q],
+                                               double lam0) {
+  double lo = -1e300, hi = 1e300;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const double b = geq[i] + dsp[i];
+    if (dh[i] > 0.0) hi = fmin(hi, 1.0 + b / dh[i]);
+    else if (dh[i] < 0.0) lo = fmax(lo, 1.0 + b / dh[i]);
+    else if (!(b > 0.0)) return lam0;
+  }
+  if (!(lo < hi)) return lam0;
+  double lam = (lam0 > lo && lam0 < hi) ? lam0 : (lo > -1e299 && hi < 1e299 ? 0.5 * (lo + hi) : lam0);
+  if (!(lam > lo && lam < hi)) return lam0;
+  for (int it = 0; it < 60; ++it) {
+    double f = 0.0, fp = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const double A = geq[i] + dsp[i] + (1.0 - lam) * dh[i];
+      f += dh[i] * log(A / w_of(i));
+      fp -= dh[i] * dh[i] / A;
+    }
+    if (f > 0.0) lo = lam; else hi = lam;
+    double nl = lam - f / fp;
+    if (!(nl > lo && nl < hi)) nl = (lo > -1e299 && hi < 1e299) ? 0.5 * (lo + hi) : lam0;
+    if (fabs(nl - lam) <= 1e-14 * fmax(1.0, fabs(lam))) return nl;
+    lam = nl;
+  }
+  return lam;
+}
 
 // c_i . v for all 27 velocities from 9 (cy, cz) partial sums.
 template <typename R>
@@ -118,7 +153,20 @@ __device__ __forceinline__ bool collide_node(R (&g)[Q], const Sym6<R>& T, const 
         num += dh * (k.K3[i] * ca.d[i] + k.L[i]);
         den += dh * (dh * k.M[i]);
       }
-      if (den > k.theta2) kappa = num / den;
+      if (den > k.theta2) {
+        kappa = num / den;
+        if (k.root) {
+          double geq[Q], dsp[Q], dhd[Q];
+          const Dots<R> cjd(jx, jy, jz), cad(ax, ay, az);
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            geq[i] = (double)phi * (double)k.E[i];
+            dsp[i] = 3.0 * w_of(i) * (double)cad.d[i];
+            dhd[i] = (double)g[i] - geq[i] - 3.0 * w_of(i) * (double)cjd.d[i];
+          }
+          kappa = R(entropy_root(geq, dsp, dhd, 1.0 + (double)kappa) - 1.0);
+        }
+      }
     }
     const R psi = (R(1) + kappa) * phi;
     const Dots<R> cb(ax + kappa * jx, ay + kappa * jy, az + kappa * jz);

@@ -63,6 +63,7 @@ def lib() -> C.CDLL:
         "elbm_set_velocity_uniform": (S, [H, D]),
         "elbm_set_source": (S, [H, P]),
         "elbm_set_source_amplitude": (S, [H, C.c_double]),
+        "elbm_set_lambda_mode": (S, [H, C.c_int32]),
         "elbm_step_source_schedule": (S, [H, D, I64]),
         "elbm_init_equilibrium": (S, [H, P, S]),
         "elbm_write_populations": (S, [H, P, S]),
@@ -196,6 +197,10 @@ def elbm_set_velocity_uniform(h, u):
 
 def elbm_set_source(h, R):
     _check(lib().elbm_set_source(h, _ptr(R)), h)
+
+
+def elbm_set_lambda_mode(h, mode):
+    _check(lib().elbm_set_lambda_mode(h, int(mode)), h)
 
 
 def elbm_set_source_amplitude(h, a):

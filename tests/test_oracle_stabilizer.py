@@ -168,3 +168,20 @@ def test_adversarial_run_stays_nonnegative():
         assert g.min().item() >= -1e-17
     assert abs(g.sum().item() - m0) / m0 < 1e-14
     assert prob.stats["fallback_nodes"] > 0
+
+
+def test_root_mode_solves_stationarity_and_tracks_closed_form():
+    """lam_mode='root' zeroes Eq. (method-entropy-root) (checked by evaluating it) and differs
+    from the closed form by O(delta)."""
+    u = torch.tensor([0.05, 0.03, 0.02], dtype=DT)
+    S = torch.as_tensor(np.linalg.inv(0.5 * np.eye(3) + 3 * np.diag([0.1, 1e-3, 1e-5])))
+    for delta, bound in ((1e-2, 5e-2), (1e-3, 5e-3)):
+        g = _state(u.numpy(), delta, 21, n=16)
+        _, a = O.collide(g, u, S, theta=0.0, lam_mode="literal", fallback=False)
+        _, b = O.collide(g, u, S, theta=0.0, lam_mode="root", fallback=False)
+        assert (a.lam - b.lam).abs().max().item() < bound
+        for n in range(16):
+            geq, dh, dsp = _split(g[:, n].numpy(), u.numpy(), S.numpy())
+            lam = b.lam[n].item()
+            res = np.sum(dh * np.log((geq + dsp + (1 - lam) * dh) / Wn))
+            assert abs(res) < 1e-14 * np.abs(dh).sum() * 50
