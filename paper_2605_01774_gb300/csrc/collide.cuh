@@ -37,11 +37,15 @@ struct PopConsts {
 };
 
 // Exact root of Eq. (method-entropy-root):
-//   f(lam) = sum_i dh_i ln((g_eq_i + ds_post_i + (1 - lam) dh_i) / W_i) = 0,
-// f decreasing (f' = -sum dh_i^2 / A_i), arguments A_i > 0 on an open bracket.  Safeguarded
-// Newton in FP64 from the closed-form lam0; returns lam0 if the bracket is empty.
+//   f(lam) = sum_i dh_i ln((g_eq_i + ds_post_i + (1 - lam) dh_i) / W_i) = 0.
+// With ln(A_i/W_i) = ln phi + ln P_i + log1p(delta_i / g_eq_i), delta_i = ds_post_i + (1 - lam) dh_i,
+// and sum dh_i = 0, sum c_i dh_i = 0, the same f is evaluated as
+//   f(lam) = sum_i dh_i (L_i + log1p(delta_i / g_eq_i)),  L_i = ln P_i - 3 c_i.u + 1.5 u.u,
+// which does not amplify the rounding of sum dh_i by ln phi.  f decreases (f' = -sum dh_i^2/A_i)
+// on the open bracket where every A_i > 0.  Safeguarded Newton in FP64 from the closed-form
+// lam0; returns lam0 if the bracket is empty.
 __device__ __forceinline__ double entropy_root(const double (&geq)[Q], const double (&dsp)[Q], const double (&dh)[Q],
-                                               double lam0) {
+                                               const double (&L)[Q], double lam0) {
   double lo = -1e300, hi = 1e300;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -57,9 +61,9 @@ __device__ __forceinline__ double entropy_root(const double (&geq)[Q], const dou
     double f = 0.0, fp = 0.0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const double A = geq[i] + dsp[i] + (1.0 - lam) * dh[i];
-      f += dh[i] * log(A / w_of(i));
-      fp -= dh[i] * dh[i] / A;
+      const double dl = dsp[i] + (1.0 - lam) * dh[i];
+      f += dh[i] * (L[i] + log1p(dl / geq[i]));
+      fp -= dh[i] * dh[i] / (geq[i] + dl);
     }
     if (f > 0.0) lo = lam; else hi = lam;
     double nl = lam - f / fp;
@@ -156,15 +160,16 @@ __device__ __forceinline__ bool collide_node(R (&g)[Q], const Sym6<R>& T, const 
       if (den > k.theta2) {
         kappa = num / den;
         if (k.root) {
-          double geq[Q], dsp[Q], dhd[Q];
+          double geq[Q], dsp[Q], dhd[Q], L[Q];
           const Dots<R> cjd(jx, jy, jz), cad(ax, ay, az);
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
             geq[i] = (double)phi * (double)k.E[i];
             dsp[i] = 3.0 * w_of(i) * (double)cad.d[i];
             dhd[i] = (double)g[i] - geq[i] - 3.0 * w_of(i) * (double)cjd.d[i];
+            L[i] = (double)k.L[i];
           }
-          kappa = R(entropy_root(geq, dsp, dhd, 1.0 + (double)kappa) - 1.0);
+          kappa = R(entropy_root(geq, dsp, dhd, L, 1.0 + (double)kappa) - 1.0);
         }
       }
     }
