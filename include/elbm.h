@@ -146,10 +146,20 @@ elbm_status elbm_set_tensor_field(elbm_handle h, const float* D6);
 elbm_status elbm_set_tensor_params_field(elbm_handle h, const float* theta6);
 
 /* Uniform velocity u (3 doubles, host).  ELBM_ERR_MACH unless every
- * P_i(u) = 1 + 3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u > 0.  For the deviation
- * storages the velocity is also the reference of the stored deviations, so it
- * may only be changed before elbm_init_* (else ELBM_ERR_STATE). */
+ * P_i(u) = 1 + 3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u > 0.  The velocity is part of the
+ * stored-state convention (deviation reference, source half-steps), so it may only
+ * be changed before elbm_init_* (else ELBM_ERR_STATE). */
 elbm_status elbm_set_velocity_uniform(elbm_handle h, const double u[3]);
+
+/* Per-node velocity u(x), FP32 [3][N] (component planes), host or device, copied by
+ * the library.  Every node collides with the equilibrium of its own velocity
+ * (Eq. method-geq), j = sum c g - phi u(x), and the stabilizer tables P_i(u(x)),
+ * ln P_i(u(x)) of Eqs. (method-lambda, method-correction) are evaluated per node
+ * (lambda = 1 where u(x) = 0 exactly).  ELBM_ERR_MACH (field discarded) if some node
+ * has a P_i(u) <= 0; only before elbm_init_* (ELBM_ERR_STATE).  The deviation storages
+ * then encode relative to the zero-velocity shape.  A source together with a velocity
+ * field is ELBM_ERR_UNSUPPORTED at elbm_step.  elbm_set_velocity_uniform removes it. */
+elbm_status elbm_set_velocity_field(elbm_handle h, const float* u3);
 
 /* Time-constant volumetric source R, FP32 [N], host or device, or NULL to
  * remove it.  Applied by the Strang split S(1/2) -> collide-stream -> S(1/2),

@@ -22,6 +22,7 @@ struct elbm_ctx {
   int cur = 0;
   void* T6 = nullptr;        // per-node T field (owned; double for FP64, else float)
   float* src = nullptr;      // per-node source (owned)
+  float* u3 = nullptr;       // per-node velocity [3][N] (owned), null = uniform u
   bool have_tensor = false;
   bool tensor_field = false;
   double D6[6] = {0, 0, 0, 0, 0, 0};
@@ -167,6 +168,7 @@ StateIO state_io(elbm_ctx* h) {
   S.pops = h->pops[h->cur];
   S.scale = h->scale[h->cur];
   S.T6 = h->tensor_field ? h->T6 : nullptr;
+  S.u3 = h->u3;
   S.src = h->src;
   S.kd = &h->kd;
   S.kf = &h->kf;
@@ -278,6 +280,7 @@ void elbm_destroy(elbm_handle h) {
   }
   cudaFree(h->T6);
   cudaFree(h->src);
+  cudaFree(h->u3);
   cudaFree(h->d_counters);
   cudaFree(h->d_scratch);
   cudaFree(h->d_out4);
@@ -338,6 +341,32 @@ elbm_status elbm_set_velocity_uniform(elbm_handle h, const double u[3]) {
   if (elbm_check_velocity(u) != ELBM_OK) return fail(h, ELBM_ERR_MACH, "velocity gives a non-positive P_i(u)");
   if (h->initialized) return fail(h, ELBM_ERR_STATE, "velocity must be set before the state is initialised");
   std::memcpy(h->u, u, sizeof(h->u));
+  if (h->u3) {
+    CK(cudaStreamSynchronize(h->stream), "sync");
+    cudaFree(h->u3);
+    h->u3 = nullptr;
+  }
+  rebuild_consts(h);
+  return ELBM_OK;
+}
+
+elbm_status elbm_set_velocity_field(elbm_handle h, const float* u3) {
+  if (!h || !u3) return fail(h, ELBM_ERR_ARG, "null argument");
+  if (h->initialized) return fail(h, ELBM_ERR_STATE, "velocity must be set before the state is initialised");
+  if (!h->u3) CK(cudaMalloc((void**)&h->u3, 3 * h->N * sizeof(float)), "cudaMalloc velocity field");
+  CK(cudaMemcpyAsync(h->u3, u3, 3 * h->N * sizeof(float), cudaMemcpyDefault, h->stream), "memcpy velocity");
+  CK(cudaMemsetAsync(h->d_counters + 1, 0, sizeof(unsigned long long), h->stream), "memset");
+  CK(launch_velocity_check(h->u3, h->N, h->d_counters + 1, h->stream), "velocity check");
+  unsigned long long bad = 0;
+  CK(cudaMemcpyAsync(&bad, h->d_counters + 1, sizeof(bad), cudaMemcpyDeviceToHost, h->stream), "memcpy");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  if (bad) {
+    cudaFree(h->u3);
+    h->u3 = nullptr;
+    return fail(h, ELBM_ERR_MACH, std::to_string(bad) + " nodes whose velocity gives a non-positive P_i(u)");
+  }
+  // the deviation storages encode relative to the zero-velocity equilibrium shape
+  h->u[0] = h->u[1] = h->u[2] = 0.0;
   rebuild_consts(h);
   return ELBM_OK;
 }
@@ -414,9 +443,12 @@ elbm_status elbm_step(elbm_handle h, int64_t nsteps) {
   if (nsteps < 0) return fail(h, ELBM_ERR_ARG, "nsteps < 0");
   if (!h->initialized) return fail(h, ELBM_ERR_STATE, "state not initialised");
   if (!h->have_tensor) return fail(h, ELBM_ERR_STATE, "no diffusion tensor set");
+  if (h->u3 && h->src)
+    return fail(h, ELBM_ERR_UNSUPPORTED, "a source with a per-node velocity field is not supported");
   StepLaunch L;
   L.prec = h->prec;
-  L.vel = (h->u[0] != 0.0 || h->u[1] != 0.0 || h->u[2] != 0.0) ? 1 : 0;
+  L.vel = h->u3 ? 2 : ((h->u[0] != 0.0 || h->u[1] != 0.0 || h->u[2] != 0.0) ? 1 : 0);
+  L.u3 = h->u3;
   L.nx = h->nx;
   L.ny = h->ny;
   L.nz = h->nz;

@@ -30,7 +30,8 @@ __device__ __forceinline__ double ld_in(const void* p, size_t idx) {
 template <typename Elem, typename Tin, int FROM_PHI>
 __global__ void __launch_bounds__(256)
 k_write(Elem* __restrict__ pops, float* __restrict__ scale, Grid G, const void* __restrict__ in,
-        const float* __restrict__ src, const PopConsts<typename Storage<Elem>::real> k) {
+        const float* __restrict__ src, const float* __restrict__ u3,
+        const PopConsts<typename Storage<Elem>::real> k) {
   using R = typename Storage<Elem>::real;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -48,12 +49,24 @@ k_write(Elem* __restrict__ pops, float* __restrict__ scale, Grid G, const void* 
     dx = dx < 0 ? G.nx - 1 : (dx >= G.nx ? 0 : dx);
     const int d = dx + G.nx * (dy + G.ny * dz);
     if (!outside) {
-      R v = FROM_PHI ? R(ld_in<Tin>(in, d)) * k.E[i] : R(ld_in<Tin>(in, (size_t)i * G.N + d));
+      R Ei = k.E[i];
+      if (FROM_PHI && u3 != nullptr) {   // equilibrium at the velocity of node d
+        const R ux = u3[d], uy = u3[G.N + d], uz = u3[2 * G.N + d];
+        const R cu = R(cx_of(i)) * ux + R(cy_of(i)) * uy + R(cz_of(i)) * uz;
+        Ei = R(w_of(i)) * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * (ux * ux + uy * uy + uz * uz));
+      }
+      R v = FROM_PHI ? R(ld_in<Tin>(in, d)) * Ei : R(ld_in<Tin>(in, (size_t)i * G.N + d));
       if (src != nullptr) v -= k.src_half * R(src[d]) * k.E[i];
       a[i] = v;
     } else {
       const int o = opp_of(i);
-      R v = FROM_PHI ? R(ld_in<Tin>(in, n)) * k.E[o] : R(ld_in<Tin>(in, (size_t)o * G.N + n));
+      R Eo = k.E[o];
+      if (FROM_PHI && u3 != nullptr) {
+        const R ux = u3[n], uy = u3[G.N + n], uz = u3[2 * G.N + n];
+        const R cu = R(cx_of(o)) * ux + R(cy_of(o)) * uy + R(cz_of(o)) * uz;
+        Eo = R(w_of(o)) * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * (ux * ux + uy * uy + uz * uz));
+      }
+      R v = FROM_PHI ? R(ld_in<Tin>(in, n)) * Eo : R(ld_in<Tin>(in, (size_t)o * G.N + n));
       if (src != nullptr) v -= k.src_half * R(src[n]) * k.E[o];
       const R phw = through_hi ? k.phi_hi : k.phi_lo;
       a[i] = R(2.0 * w_of(i)) * phw - v;
@@ -67,7 +80,8 @@ template <typename Elem, typename Tout, int WHAT>
 __global__ void __launch_bounds__(256)
 k_read(Field<Elem> f, Grid G, Tout* __restrict__ out, Tout* __restrict__ qout,
        const typename Storage<Elem>::real* __restrict__ T6,
-       const float* __restrict__ src, const PopConsts<typename Storage<Elem>::real> k) {
+       const float* __restrict__ src, const float* __restrict__ u3,
+       const PopConsts<typename Storage<Elem>::real> k) {
   using R = typename Storage<Elem>::real;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -90,7 +104,13 @@ k_read(Field<Elem> f, Grid G, Tout* __restrict__ out, Tout* __restrict__ qout,
     out[n] = Tout(phi);
     if (qout != nullptr) {
       // q = j - S j / 2 = T j / 2 with T = 2I - S (Eq. app-cube-lb-flux)
-      const R jx = mx - phi * k.ux, jy = my - phi * k.uy, jz = mz - phi * k.uz;
+      R ux = k.ux, uy = k.uy, uz = k.uz;
+      if (u3 != nullptr) {
+        ux = u3[n];
+        uy = u3[G.N + n];
+        uz = u3[2 * G.N + n];
+      }
+      const R jx = mx - phi * ux, jy = my - phi * uy, jz = mz - phi * uz;
       const Sym6<R> T = load_T<R>(T6, G.N, n, k.T);
       R tx, ty, tz;
       sym_mul(T, jx, jy, jz, tx, ty, tz);
@@ -281,11 +301,11 @@ cudaError_t write_t(const StateIO& S, const void* in, int in_f32, int from_phi, 
   Elem* p = static_cast<Elem*>(S.pops);
   const auto& k = consts_of<Elem>(S);
   if (in_f32) {
-    if (from_phi) k_write<Elem, float, 1><<<g, b, 0, s>>>(p, S.scale, G, in, S.src, k);
-    else k_write<Elem, float, 0><<<g, b, 0, s>>>(p, S.scale, G, in, S.src, k);
+    if (from_phi) k_write<Elem, float, 1><<<g, b, 0, s>>>(p, S.scale, G, in, S.src, S.u3, k);
+    else k_write<Elem, float, 0><<<g, b, 0, s>>>(p, S.scale, G, in, S.src, S.u3, k);
   } else {
-    if (from_phi) k_write<Elem, double, 1><<<g, b, 0, s>>>(p, S.scale, G, in, S.src, k);
-    else k_write<Elem, double, 0><<<g, b, 0, s>>>(p, S.scale, G, in, S.src, k);
+    if (from_phi) k_write<Elem, double, 1><<<g, b, 0, s>>>(p, S.scale, G, in, S.src, S.u3, k);
+    else k_write<Elem, double, 0><<<g, b, 0, s>>>(p, S.scale, G, in, S.src, S.u3, k);
   }
   return cudaGetLastError();
 }
@@ -299,11 +319,11 @@ cudaError_t read_t(const StateIO& S, void* out, void* q, int out_f32, int what, 
   Field<Elem> f = field_of<Elem>(S);
   const R* T6 = static_cast<const R*>(S.T6);
   if (out_f32) {
-    if (what == 0) k_read<Elem, float, 0><<<g, b, 0, s>>>(f, G, (float*)out, (float*)q, T6, S.src, k);
-    else k_read<Elem, float, 1><<<g, b, 0, s>>>(f, G, (float*)out, (float*)q, T6, S.src, k);
+    if (what == 0) k_read<Elem, float, 0><<<g, b, 0, s>>>(f, G, (float*)out, (float*)q, T6, S.src, S.u3, k);
+    else k_read<Elem, float, 1><<<g, b, 0, s>>>(f, G, (float*)out, (float*)q, T6, S.src, S.u3, k);
   } else {
-    if (what == 0) k_read<Elem, double, 0><<<g, b, 0, s>>>(f, G, (double*)out, (double*)q, T6, S.src, k);
-    else k_read<Elem, double, 1><<<g, b, 0, s>>>(f, G, (double*)out, (double*)q, T6, S.src, k);
+    if (what == 0) k_read<Elem, double, 0><<<g, b, 0, s>>>(f, G, (double*)out, (double*)q, T6, S.src, S.u3, k);
+    else k_read<Elem, double, 1><<<g, b, 0, s>>>(f, G, (double*)out, (double*)q, T6, S.src, S.u3, k);
   }
   return cudaGetLastError();
 }
@@ -354,6 +374,25 @@ cudaError_t launch_reduce(const StateIO& S, double* scratch, double* out4, cudaS
     case 3: return reduce_t<__nv_bfloat16>(S, scratch, out4, s);
   }
   return cudaErrorInvalidValue;
+}
+
+__global__ void k_velocity_check(const float* __restrict__ u3, size_t N, unsigned long long* bad) {
+  const size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const double ux = u3[n], uy = u3[N + n], uz = u3[2 * N + n];
+  bool ok = isfinite(ux) && isfinite(uy) && isfinite(uz);
+  const double uu = ux * ux + uy * uy + uz * uz;
+  for (int i = 0; i < Q && ok; ++i) {
+    const double cu = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
+    ok = 1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu > 0.0;
+  }
+  if (!ok) atomicAdd(bad, 1ull);
+}
+
+cudaError_t launch_velocity_check(const float* u3, size_t N, unsigned long long* bad, cudaStream_t s) {
+  const int b = 256;
+  k_velocity_check<<<(unsigned)((N + b - 1) / b), b, 0, s>>>(u3, N, bad);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_tensor_prepass(const float* in, int is_params, void* T6, int t6_f64, size_t N,

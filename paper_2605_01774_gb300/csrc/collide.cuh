@@ -116,12 +116,40 @@ __device__ __forceinline__ void moments(const R (&g)[Q], R& phi, R& mx, R& my, R
   mz = (dz[0] + dz[1] + dz[2]) + (dz[3] + dz[4] + dz[5]) + (dz[6] + dz[7] + dz[8]);
 }
 
-// VEL = 0: u = 0 exactly (kappa = 0); VEL = 1: uniform u from PopConsts.
+// P_i(u) tables of one node (per-node velocity fields).
+template <typename R>
+__device__ __forceinline__ void node_tables(PopConsts<R>& kn, R ux, R uy, R uz) {
+  const R uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const R cu = R(cx_of(i)) * ux + R(cy_of(i)) * uy + R(cz_of(i)) * uz;
+    const R P = R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu;
+    kn.E[i] = R(w_of(i)) * P;
+    kn.K3[i] = R(3) * (R(1) / P - R(1));
+    kn.L[i] = log(P) - R(3) * cu + R(1.5) * uu;
+    kn.M[i] = R(1) / (R(w_of(i)) * P);
+  }
+  kn.ux = ux;
+  kn.uy = uy;
+  kn.uz = uz;
+}
+
+// VEL = 0: u = 0 exactly (kappa = 0); VEL = 1: uniform u from PopConsts; VEL = 2: the
+// node's own velocity un[3] (tables rebuilt per node; lambda = 1 where that u is exactly 0).
 // Returns true if the positivity fallback was taken; phi_out receives the node's phi,
 // which the collision conserves exactly.
 template <typename R, int VEL>
 __device__ __forceinline__ bool collide_node(R (&g)[Q], const Sym6<R>& T, const PopConsts<R>& k,
-                                             bool fallback, R& phi_out) {
+                                             bool fallback, R& phi_out, const R* un = nullptr) {
+  if constexpr (VEL == 2) {
+    PopConsts<R> kn = k;
+    if (un[0] == R(0) && un[1] == R(0) && un[2] == R(0)) {
+      node_tables(kn, R(0), R(0), R(0));
+      return collide_node<R, 0>(g, T, kn, fallback, phi_out);
+    }
+    node_tables(kn, un[0], un[1], un[2]);
+    return collide_node<R, 1>(g, T, kn, fallback, phi_out);
+  }
   R phi, mx, my, mz;
   moments(g, phi, mx, my, mz);
   phi_out = phi;

@@ -11,7 +11,8 @@ namespace elbm {
 
 struct StepLaunch {
   int prec;                     // elbm_precision
-  int vel;                      // 0: u = 0, 1: uniform u
+  int vel;                      // 0: u = 0, 1: uniform u, 2: per-node u field
+  const float* u3;              // per-node velocity [3][N] (vel = 2), else null
   int nx, ny, nz;
   size_t N;
   int dirichlet, fallback;
@@ -35,6 +36,7 @@ struct StateIO {
   void* pops;                   // storage buffer (read: const)
   float* scale;
   const void* T6;               // double for FP64, else float
+  const float* u3;              // per-node velocity [3][N] or null
   const float* src;
   const PopConsts<double>* kd;
   const PopConsts<float>* kf;
@@ -45,6 +47,9 @@ cudaError_t launch_read_state(const StateIO& S, void* out, void* q_out, int out_
 // partials: scratch of >= reduce_blocks(N) * 4 doubles; out4: device (mass, entropy, gmin, nonfinite count)
 size_t reduce_blocks(const StateIO& S);
 cudaError_t launch_reduce(const StateIO& S, double* scratch, double* out4, cudaStream_t s);
+
+// Count nodes of a [3][N] velocity field with some P_i(u) <= 0 or a non-finite component.
+cudaError_t launch_velocity_check(const float* u3, size_t N, unsigned long long* bad, cudaStream_t s);
 
 // Tensor pre-pass: D6 or theta6 (float [6][N]) -> T6 ([6][N], double if t6_f64 else float);
 // bad_count counts non-SPD nodes.

@@ -19,8 +19,8 @@ template <typename Elem, int VEL>
 __global__ void __launch_bounds__(256, step_min_blocks<Elem>())
 k_step(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G,
        const typename Storage<Elem>::real* __restrict__ T6,
-       const float* __restrict__ src, int fallback, unsigned long long* __restrict__ counters,
-       const PopConsts<typename Storage<Elem>::real> k) {
+       const float* __restrict__ src, const float* __restrict__ u3, int fallback,
+       unsigned long long* __restrict__ counters, const PopConsts<typename Storage<Elem>::real> k) {
   using R = typename Storage<Elem>::real;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -38,7 +38,12 @@ k_step(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G
     }
     const Sym6<R> T = load_T<R>(T6, G.N, n, k.T);
     R phi;
-    took = collide_node<R, VEL>(g, T, k, fallback != 0, phi);
+    if constexpr (VEL == 2) {
+      const R un[3] = {R(__ldg(u3 + n)), R(__ldg(u3 + G.N + n)), R(__ldg(u3 + 2 * G.N + n))};
+      took = collide_node<R, 2>(g, T, k, fallback != 0, phi, un);
+    } else {
+      took = collide_node<R, VEL>(g, T, k, fallback != 0, phi);
+    }
     Storage<Elem>::store(pout, sout, G.N, n, g, k.E, phi);
   }
   const unsigned m = __ballot_sync(0xffffffffu, took);
@@ -60,17 +65,22 @@ static cudaError_t launch_t(const StepLaunch& L, cudaStream_t s) {
   const PopConsts<R>& k = *reinterpret_cast<const PopConsts<R>*>(std::is_same<R, double>::value ? (const void*)L.kd
                                                                                                : (const void*)L.kf);
   k_step<Elem, VEL><<<g, b, 0, s>>>(in, static_cast<Elem*>(L.pout), L.sout, G, static_cast<const R*>(L.T6), L.src,
-                                    L.fallback, L.counters, k);
+                                    L.u3, L.fallback, L.counters, k);
   return cudaGetLastError();
 }
 
+template <typename Elem>
+static cudaError_t launch_v(const StepLaunch& L, cudaStream_t s) {
+  if (L.vel == 2) return launch_t<Elem, 2>(L, s);
+  return L.vel ? launch_t<Elem, 1>(L, s) : launch_t<Elem, 0>(L, s);
+}
+
 cudaError_t launch_step(const StepLaunch& L, cudaStream_t s) {
-  const bool v = L.vel != 0;
   switch (L.prec) {
-    case 0: return v ? launch_t<double, 1>(L, s) : launch_t<double, 0>(L, s);
-    case 1: return v ? launch_t<float, 1>(L, s) : launch_t<float, 0>(L, s);
-    case 2: return v ? launch_t<__half, 1>(L, s) : launch_t<__half, 0>(L, s);
-    case 3: return v ? launch_t<__nv_bfloat16, 1>(L, s) : launch_t<__nv_bfloat16, 0>(L, s);
+    case 0: return launch_v<double>(L, s);
+    case 1: return launch_v<float>(L, s);
+    case 2: return launch_v<__half>(L, s);
+    case 3: return launch_v<__nv_bfloat16>(L, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -61,6 +61,7 @@ def lib() -> C.CDLL:
         "elbm_set_tensor_field": (S, [H, P]),
         "elbm_set_tensor_params_field": (S, [H, P]),
         "elbm_set_velocity_uniform": (S, [H, D]),
+        "elbm_set_velocity_field": (S, [H, P]),
         "elbm_set_source": (S, [H, P]),
         "elbm_set_source_amplitude": (S, [H, C.c_double]),
         "elbm_set_lambda_mode": (S, [H, C.c_int32]),
@@ -193,6 +194,10 @@ def elbm_set_tensor_params_field(h, theta6):
 
 def elbm_set_velocity_uniform(h, u):
     _check(lib().elbm_set_velocity_uniform(h, _d(u, 3)), h)
+
+
+def elbm_set_velocity_field(h, u3):
+    _check(lib().elbm_set_velocity_field(h, _ptr(u3)), h)
 
 
 def elbm_set_source(h, R):

@@ -277,3 +277,41 @@ def test_exact_entropy_root_mode(E, prec, bound):
     print(f"root mode {prec}: rel L2 vs oracle root {err:.2e}; root vs closed form {rel_l2(ref, ref_cf):.2e}")
     assert err < bound
     assert rel_l2(ref, ref_cf) > 10 * bound or prec == "f32"
+
+
+@pytest.mark.parametrize("prec,bound", [("f64", 1e-12), ("f32", 1e-6), ("f16dev", 2e-4)])
+def test_velocity_field(E, prec, bound):
+    """Per-node velocity u(x) (some nodes exactly 0), rotated tensor, 6 steps: populations and
+    the flux read-out q = j - S j / 2 against the oracle with the same field."""
+    dims = (10, 8, 6)
+    rng = synth.rng(31)
+    x, y, z = synth.grid(dims)
+    u = np.stack([0.04 * np.sin(2 * np.pi * y / 8), 0.03 * np.cos(2 * np.pi * z / 6), 0.02 * np.sin(2 * np.pi * x / 10)])
+    u[:, 0, 0, :] = 0.0
+    u = u.astype(np.float32).astype(np.float64)
+    D = synth.tensor_from_principal((0.05, 0.01, 0.002), synth.rot_zyz(*synth.haar_euler(rng)))
+    phi0 = 1.0 + 0.3 * synth.gaussian(dims, (4.5, 3.5, 2.5), 2.0)
+    lat = gpu_lattice(E, dims, prec, D=D, theta=1e-8 if prec == "f64" else 3e-4)
+    E.elbm_set_velocity_field(lat.h, torch.as_tensor(u, dtype=torch.float32, device="cuda"))
+    E.elbm_init_equilibrium(lat.h, torch.as_tensor(phi0, device="cuda"))
+    E.elbm_step(lat.h, 6)
+    g = read_pops(E, lat)
+    phi = torch.empty(dims[::-1], dtype=torch.float64, device="cuda")
+    q = torch.empty((3,) + dims[::-1], dtype=torch.float64, device="cuda")
+    E.elbm_read_moments(lat.h, phi, q)
+    torch.cuda.synchronize()
+    ut = torch.as_tensor(u)
+    prob = O.Problem(u=ut, S=O.relaxation_matrix(torch.as_tensor(D)), theta=1e-8 if prec == "f64" else 3e-4)
+    ref = O.run(O.init_equilibrium(phi0, ut), prob, 6)
+    qref = O.flux_q(ref, ut, prob.S)
+    err, qerr = rel_l2(g, ref), rel_l2(q.cpu(), qref)
+    print(f"velocity field {prec}: rel L2 pops {err:.2e}, flux {qerr:.2e}")
+    assert err < bound
+    assert qerr < max(bound, 1e-9) * 1e3
+    # invalid fields are rejected
+    bad = torch.zeros((3,) + dims[::-1], dtype=torch.float32, device="cuda")
+    bad[0, 0, 0, 0] = 0.9
+    lat2 = E.Lattice(dims, prec)
+    with pytest.raises(E.ElbmError) as ei:
+        E.elbm_set_velocity_field(lat2.h, bad)
+    assert ei.value.status == 3
