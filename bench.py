@@ -311,12 +311,20 @@ def run_ours(args, rank, world, local, dist):
     return line
 
 
+def shard(items, rank, world):
+    """Round-robin share of independent units for one rank (every unit exactly once)."""
+    return items[rank::world]
+
+
 def run_batched(args, E, dev, dist, world):
     """Orientation / anisotropy sweep: 512 periodic domains, edges U{16..96} (seed 4),
     FP32, u = 0; persistent graph-captured kernel (autotuned) vs one batched launch per
-    step in a graph vs one plain launch per domain per step."""
+    step in a graph vs one plain launch per domain per step.  With several ranks the
+    domains are shared round-robin (independent problems: no data-path collective)."""
     import torch
     table, _ = synth.batched_domains()
+    rank = dist.get_rank() if dist is not None else 0
+    table = shard(table, rank, world)
     edges = [d["n"] for d in table]
     D6 = np.stack([synth.d6_from_matrix(d["D"]) for d in table])
     phi0 = torch.as_tensor(np.concatenate([synth.batched_phi0(n).ravel() for n in edges]).astype(np.float32),
@@ -325,7 +333,9 @@ def run_batched(args, E, dev, dist, world):
     E.elbm_batch_init_equilibrium(h, phi0)
     tile, bps = E.elbm_batch_autotune(h, 2)
     total = E.elbm_batch_info(h)["total_nodes"]
-    out = {"domains": len(edges), "nodes": total, "steps": args.batched_steps, "tile": tile,
+    all_nodes = sum_over_ranks(float(total), dist, dev)
+    out = {"domains": len(synth.batched_domains()[0]), "nodes": int(all_nodes), "steps": args.batched_steps,
+           "tile": tile,
            "blocks_per_sm": bps, "bytes_per_node": BYTES_PER_NODE["f32"]}
     peak, _ = measured_peaks()
     for mode, name in ((0, "persistent_graph"), (1, "per_step_graph"), (2, "per_domain_launches")):
@@ -337,7 +347,7 @@ def run_batched(args, E, dev, dist, world):
         E.elbm_batch_step(h, args.batched_steps, mode)
         E.elbm_batch_synchronize(h)
         dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
-        mlups = world * total * args.batched_steps / dt / 1e6
+        mlups = all_nodes * args.batched_steps / dt / 1e6
         out[name] = {"ms_per_step": dt * 1e3 / args.batched_steps, "mlups": mlups,
                      "hbm_frac_of_measured": mlups * 1e6 * BYTES_PER_NODE["f32"] / 1e9 / peak}
     out["persistent_in_graph"] = E.elbm_batch_info(h)["persistent_in_graph"]
