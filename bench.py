@@ -38,7 +38,7 @@ UNIT = "MLUPS"
 BYTES_PER_NODE = {"f64": 27 * 8 * 2, "f32": 27 * 4 * 2, "f16dev": (27 * 2 + 4) * 2, "bf16dev": (27 * 2 + 4) * 2}
 WORKLOAD = ("advected anisotropic Gaussian plume 256^3 periodic, u=(0.05,0.03,0.02), "
             "D=R diag(0.1,1e-3,1e-5) R^T (seeded ZYZ, seed 2), sigma0=8")
-KERNEL_SOURCES = ["collide.cuh", "storage.cuh", "pull.cuh", "step.cu", "lattice.cuh"]
+KERNEL_SOURCES = ["collide.cuh", "storage.cuh", "pull.cuh", "step.cu", "step_rows.cu", "bulk.cuh", "lattice.cuh"]
 THETA = 3e-4   # stabilizer guard used by every form, so the forms differ only in arithmetic and storage
 
 
@@ -176,6 +176,7 @@ def run_ours(args, rank, world, local, dist):
         E.elbm_set_tensor_uniform(lat.h, D6)
         E.elbm_set_velocity_uniform(lat.h, wl.u)
         E.elbm_set_params(lat.h, theta=THETA)
+        E.elbm_set_step_kernel(lat.h, args.step_kernel)
         stream.wait_stream(torch.cuda.current_stream(dev))
         E.elbm_init_equilibrium(lat.h, phi0)
         return lat
@@ -258,6 +259,7 @@ def run_ours(args, rank, world, local, dist):
     lat = E.Lattice(wl.dims, headline, stream=stream)
     E.elbm_set_tensor_uniform(lat.h, D6)
     E.elbm_set_velocity_uniform(lat.h, wl.u)
+    E.elbm_set_step_kernel(lat.h, args.step_kernel)
     E.elbm_init_equilibrium(lat.h, host_phi0)
     E.elbm_step(lat.h, args.warmup)
     stream.synchronize()
@@ -295,7 +297,7 @@ def run_ours(args, rank, world, local, dist):
                    "l2_flush": "inputs larger than L2: %.2f GB per population buffer" %
                                (hf["bytes_per_node"] / 2 * N / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "err_steps": ek},
+                   "err_steps": ek, "step_kernel": args.step_kernel},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                      "algorithmic_bytes_per_node": hf["bytes_per_node"], "kernel": "k_step"},
@@ -420,6 +422,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=100,
                     help="steps per mode of the 512-domain sweep (0 skips it)")
+    ap.add_argument("--step-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="step implementation: 0 auto, 1 per-node gathers, 2 staged rows")
     ap.add_argument("--only", default=None, choices=["f16dev", "bf16dev", "f32", "f64"],
                     help="time one form only (profiling runs)")
     args = ap.parse_args()

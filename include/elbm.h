@@ -125,6 +125,22 @@ elbm_status elbm_set_params(elbm_handle h, const elbm_params* p);
  * ELBM_ERR_ARG for other modes. */
 elbm_status elbm_set_lambda_mode(elbm_handle h, int32_t mode);
 
+/* Which implementation of the fused collide-stream step (Eq. method-lbe with the collision
+ * of Eqs. method-split..method-fallback) elbm_step launches; all give the same result up to
+ * the order of floating-point operations, which is identical (bit-equal outputs).
+ *   0 (default) auto: 2 for the 16-bit deviation storages where available, else 1 (the
+ *     faster of the two for each storage on the 256^3 advected-plume workload).
+ *   1 one thread per node gathering its 27 pulled populations from global memory.
+ *   2 persistent blocks taking x-rows from a ticket counter and staging each row's 27
+ *     pulled source rows (and, for the deviation storages, the 9 scale rows) in shared
+ *     memory with asynchronous bulk copies, two buffers deep; needs nx % 8 == 0 and the
+ *     buffers within 200 KiB: nx <= 472 in FP64, 944 in FP32, 1136 in the deviation
+ *     storages.
+ * ELBM_ERR_ARG for other values, ELBM_ERR_UNSUPPORTED for 2 where it is not available.
+ * A bounded staging wait that gives up makes the next elbm_synchronize or elbm_reduce
+ * return ELBM_ERR_TIMEOUT. */
+elbm_status elbm_set_step_kernel(elbm_handle h, int32_t variant);
+
 /* --------------------------------------------------------- problem data */
 
 /* Uniform tensor D, 6 doubles (Dxx, Dxy, Dxz, Dyy, Dyz, Dzz), host memory.

@@ -37,6 +37,7 @@ struct elbm_ctx {
   bool initialized = false;
   double src_amp = 1.0;      // source amplitude of the most recent half-step a_{n-1}
   int lambda_mode = 0;       // 0 closed form, 1 exact root
+  int step_kernel = 0;       // 0 auto, 1 per-node gathers, 2 staged rows
   std::string err;
 };
 
@@ -257,10 +258,10 @@ elbm_status elbm_create(const int64_t dims[3], elbm_precision prec, const elbm_b
     if (e == cudaSuccess && is_dev_format(h->prec)) e = cudaMalloc((void**)&h->scale[b], h->N * sizeof(float));
   }
   StateIO S = state_io(h);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_counters, 4 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_counters, 8 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_scratch, reduce_blocks(S) * 4 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_out4, 4 * sizeof(double));
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_counters, 0, 4 * sizeof(unsigned long long), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_counters, 0, 8 * sizeof(unsigned long long), h->stream);
   if (e != cudaSuccess) {
     elbm_status s = e == cudaErrorMemoryAllocation ? ELBM_ERR_OOM : ELBM_ERR_CUDA;
     elbm_destroy(h);
@@ -460,6 +461,7 @@ elbm_status elbm_step(elbm_handle h, int64_t nsteps) {
   L.counters = h->d_counters;
   L.kd = &h->kd;
   L.kf = &h->kf;
+  L.variant = h->step_kernel;
   for (int64_t s = 0; s < nsteps; ++s) {
     L.pin = h->pops[h->cur];
     L.sin = h->scale[h->cur];
@@ -476,6 +478,26 @@ elbm_status elbm_set_lambda_mode(elbm_handle h, int32_t mode) {
   if (!h || (mode != 0 && mode != 1)) return fail(h, ELBM_ERR_ARG, "mode must be 0 or 1");
   h->lambda_mode = mode;
   rebuild_consts(h);
+  return ELBM_OK;
+}
+
+elbm_status elbm_set_step_kernel(elbm_handle h, int32_t variant) {
+  if (!h || variant < 0 || variant > 2) return fail(h, ELBM_ERR_ARG, "variant must be 0, 1 or 2");
+  if (variant == 2 && !rows_eligible(h->prec, h->nx))
+    return fail(h, ELBM_ERR_UNSUPPORTED, "staged-row step needs nx % 8 == 0 and rows that fit in shared memory");
+  h->step_kernel = variant;
+  return ELBM_OK;
+}
+
+// A staging wait of the step kernel gave up (counters[2]); clears the flag.
+static elbm_status check_timeout(elbm_ctx* h) {
+  unsigned long long t = 0;
+  CK(cudaMemcpyAsync(&t, h->d_counters + 2, sizeof(t), cudaMemcpyDeviceToHost, h->stream), "memcpy");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  if (t != 0) {
+    CK(cudaMemsetAsync(h->d_counters + 2, 0, sizeof(t), h->stream), "memset");
+    return fail(h, ELBM_ERR_TIMEOUT, "a staging wait in the step kernel ran out");
+  }
   return ELBM_OK;
 }
 
@@ -521,6 +543,7 @@ elbm_status elbm_reduce(elbm_handle h, double* mass, double* entropy, double* gm
   if (entropy) *entropy = o[1];
   if (gmin) *gmin = o[2];
   if (n_fallback) *n_fallback = (int64_t)fb;
+  if (check_timeout(h) != ELBM_OK) return ELBM_ERR_TIMEOUT;
   if (o[3] > 0) return fail(h, ELBM_ERR_NONFINITE, std::to_string((long long)o[3]) + " non-finite populations");
   return ELBM_OK;
 }
@@ -535,7 +558,7 @@ elbm_status elbm_synchronize(elbm_handle h) {
   if (!h) return ELBM_ERR_ARG;
   CK(cudaStreamSynchronize(h->stream), "sync");
   CK(cudaGetLastError(), "async error");
-  return ELBM_OK;
+  return check_timeout(h);
 }
 
 static size_t ckpt_bytes(elbm_ctx* h) {

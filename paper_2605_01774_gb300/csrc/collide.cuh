@@ -33,7 +33,8 @@ struct PopConsts {
   Sym6<R> T;         // uniform T = 2I - S
   R src_step;        // source multiplier of this step: (a_{n-1} + a_n)/2 (merged Strang halves)
   R src_half;        // half-step multiplier of the stored state: a_{n-1}/2
-  int root;          // 1: lambda from the exact entropy-stationarity root (FP64 Newton)
+  int root;          // 1: lambda from the exact entropy-stationarity root (FP64 Newton); selects
+                     // the ROOT instantiation of the step kernels
 };
 
 // Exact root of Eq. (method-entropy-root):
@@ -136,9 +137,11 @@ __device__ __forceinline__ void node_tables(PopConsts<R>& kn, R ux, R uy, R uz) 
 
 // VEL = 0: u = 0 exactly (kappa = 0); VEL = 1: uniform u from PopConsts; VEL = 2: the
 // node's own velocity un[3] (tables rebuilt per node; lambda = 1 where that u is exactly 0).
+// ROOT: lambda from the exact entropy root (k.root); a separate instantiation, so the FP64
+// Newton arrays cost the closed-form kernels no registers.
 // Returns true if the positivity fallback was taken; phi_out receives the node's phi,
 // which the collision conserves exactly.
-template <typename R, int VEL>
+template <typename R, int VEL, bool ROOT = false>
 __device__ __forceinline__ bool collide_node(R (&g)[Q], const Sym6<R>& T, const PopConsts<R>& k,
                                              bool fallback, R& phi_out, const R* un = nullptr) {
   if constexpr (VEL == 2) {
@@ -148,7 +151,7 @@ __device__ __forceinline__ bool collide_node(R (&g)[Q], const Sym6<R>& T, const 
       return collide_node<R, 0>(g, T, kn, fallback, phi_out);
     }
     node_tables(kn, un[0], un[1], un[2]);
-    return collide_node<R, 1>(g, T, kn, fallback, phi_out);
+    return collide_node<R, 1, ROOT>(g, T, kn, fallback, phi_out);
   }
   R phi, mx, my, mz;
   moments(g, phi, mx, my, mz);
@@ -187,7 +190,7 @@ __device__ __forceinline__ bool collide_node(R (&g)[Q], const Sym6<R>& T, const 
       }
       if (den > k.theta2) {
         kappa = num / den;
-        if (k.root) {
+        if constexpr (ROOT) {
           double geq[Q], dsp[Q], dhd[Q], L[Q];
           const Dots<R> cjd(jx, jy, jz), cad(ax, ay, az);
 #pragma unroll

@@ -22,11 +22,15 @@ struct StepLaunch {
   float* sout;
   const void* T6;               // per-node T = 2I - S [6][N] (double for FP64, else float) or null
   const float* src;             // per-node source [N] or null
-  unsigned long long* counters; // [0] fallback count
+  unsigned long long* counters; // [0] fallback count, [2] staging wait ran out, [4..5] row tickets
   const PopConsts<double>* kd;  // host copies, passed by value to the kernel
   const PopConsts<float>* kf;
+  int variant;                  // 0 auto, 1 one thread per node with global gathers, 2 staged rows
 };
 cudaError_t launch_step(const StepLaunch& L, cudaStream_t s);
+// Staged-row kernel (step_rows.cu): usable when rows_eligible(prec, nx); else cudaErrorNotSupported.
+bool rows_eligible(int prec, int nx);
+cudaError_t launch_step_rows(const StepLaunch& L, cudaStream_t s);
 
 // State transfer.  mode 0: populations [27][N] <-> caller; mode 1: phi0 [N] -> equilibrium.
 struct StateIO {

@@ -15,7 +15,7 @@ constexpr int step_min_blocks() {
   return std::is_same<Elem, double>::value ? 1 : ELBM_STEP_MINB;
 }
 
-template <typename Elem, int VEL>
+template <typename Elem, int VEL, bool ROOT>
 __global__ void __launch_bounds__(256, step_min_blocks<Elem>())
 k_step(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G,
        const typename Storage<Elem>::real* __restrict__ T6,
@@ -40,9 +40,9 @@ k_step(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G
     R phi;
     if constexpr (VEL == 2) {
       const R un[3] = {R(__ldg(u3 + n)), R(__ldg(u3 + G.N + n)), R(__ldg(u3 + 2 * G.N + n))};
-      took = collide_node<R, 2>(g, T, k, fallback != 0, phi, un);
+      took = collide_node<R, 2, ROOT>(g, T, k, fallback != 0, phi, un);
     } else {
-      took = collide_node<R, VEL>(g, T, k, fallback != 0, phi);
+      took = collide_node<R, VEL, ROOT>(g, T, k, fallback != 0, phi);
     }
     Storage<Elem>::store(pout, sout, G.N, n, g, k.E, phi);
   }
@@ -55,7 +55,7 @@ static dim3 block_for(int nx) {
   return dim3(bx, 256 / bx, 1);
 }
 
-template <typename Elem, int VEL>
+template <typename Elem, int VEL, bool ROOT>
 static cudaError_t launch_t(const StepLaunch& L, cudaStream_t s) {
   using R = typename Storage<Elem>::real;
   Field<Elem> in{static_cast<const Elem*>(L.pin), L.sin};
@@ -64,18 +64,29 @@ static cudaError_t launch_t(const StepLaunch& L, cudaStream_t s) {
   dim3 g((L.nx + b.x - 1) / b.x, (L.ny + b.y - 1) / b.y, L.nz);
   const PopConsts<R>& k = *reinterpret_cast<const PopConsts<R>*>(std::is_same<R, double>::value ? (const void*)L.kd
                                                                                                : (const void*)L.kf);
-  k_step<Elem, VEL><<<g, b, 0, s>>>(in, static_cast<Elem*>(L.pout), L.sout, G, static_cast<const R*>(L.T6), L.src,
+  k_step<Elem, VEL, ROOT><<<g, b, 0, s>>>(in, static_cast<Elem*>(L.pout), L.sout, G, static_cast<const R*>(L.T6), L.src,
                                     L.u3, L.fallback, L.counters, k);
   return cudaGetLastError();
 }
 
 template <typename Elem>
 static cudaError_t launch_v(const StepLaunch& L, cudaStream_t s) {
-  if (L.vel == 2) return launch_t<Elem, 2>(L, s);
-  return L.vel ? launch_t<Elem, 1>(L, s) : launch_t<Elem, 0>(L, s);
+  // the exact root applies only where u != 0 (kappa = 0 at u = 0)
+  const bool root = (std::is_same<Elem, double>::value ? L.kd->root : L.kf->root) != 0;
+  if (L.vel == 2) return root ? launch_t<Elem, 2, true>(L, s) : launch_t<Elem, 2, false>(L, s);
+  if (L.vel == 1) return root ? launch_t<Elem, 1, true>(L, s) : launch_t<Elem, 1, false>(L, s);
+  return launch_t<Elem, 0, false>(L, s);
 }
 
 cudaError_t launch_step(const StepLaunch& L, cudaStream_t s) {
+  // auto: the staged-row kernel for the 16-bit deviation storages (where it measured at
+  // least as fast), the per-node kernel for FP32 and FP64 (faster there)
+  const bool rows = L.variant == 2 || (L.variant == 0 && L.prec >= 2);
+  if (rows && rows_eligible(L.prec, L.nx)) {
+    const cudaError_t e = launch_step_rows(L, s);
+    if (e != cudaErrorNotSupported || L.variant == 2) return e;
+  }
+  if (L.variant == 2) return cudaErrorNotSupported;
   switch (L.prec) {
     case 0: return launch_v<double>(L, s);
     case 1: return launch_v<float>(L, s);

@@ -65,6 +65,7 @@ def lib() -> C.CDLL:
         "elbm_set_source": (S, [H, P]),
         "elbm_set_source_amplitude": (S, [H, C.c_double]),
         "elbm_set_lambda_mode": (S, [H, C.c_int32]),
+        "elbm_set_step_kernel": (S, [H, C.c_int32]),
         "elbm_step_source_schedule": (S, [H, D, I64]),
         "elbm_init_equilibrium": (S, [H, P, S]),
         "elbm_write_populations": (S, [H, P, S]),
@@ -206,6 +207,10 @@ def elbm_set_source(h, R):
 
 def elbm_set_lambda_mode(h, mode):
     _check(lib().elbm_set_lambda_mode(h, int(mode)), h)
+
+
+def elbm_set_step_kernel(h, variant):
+    _check(lib().elbm_set_step_kernel(h, int(variant)), h)
 
 
 def elbm_set_source_amplitude(h, a):
