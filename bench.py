@@ -219,11 +219,13 @@ def run_ours(args, rank, world, local, dist):
         if prec == headline:
             clocks = ck
         d = E.elbm_reduce(lat.h, allow_nonfinite=True)
+        proj = E.elbm_storage_projections(lat.h)
         lat.close()
         ms_max = max_over_ranks(ms, dist, dev)
         forms[prec] = dict(ms_per_step=ms_max / args.steps,
                            mlups=world * N * args.steps / (ms_max * 1e-3) / 1e6,
-                           bytes_per_node=BYTES_PER_NODE[prec], n_fallback=d["n_fallback"])
+                           bytes_per_node=BYTES_PER_NODE[prec], n_fallback=d["n_fallback"],
+                           n_projected=proj, finite=d["status"] == 0)
     # FP64: ALU-bound on this part; fewer steps keep the run short
     k64 = max(10, min(args.steps, 200))
     lat = make("f64")

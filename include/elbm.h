@@ -128,8 +128,8 @@ elbm_status elbm_set_lambda_mode(elbm_handle h, int32_t mode);
 /* Which implementation of the fused collide-stream step (Eq. method-lbe with the collision
  * of Eqs. method-split..method-fallback) elbm_step launches; all give the same result up to
  * the order of floating-point operations, which is identical (bit-equal outputs).
- *   0 (default) auto: 2 for the 16-bit deviation storages where available, else 1 (the
- *     faster of the two for each storage on the 256^3 advected-plume workload).
+ *   0 (default) auto: 1, which measured at least as fast as 2 for every storage on the
+ *     256^3 advected-plume workload.
  *   1 one thread per node gathering its 27 pulled populations from global memory.
  *   2 persistent blocks taking x-rows from a ticket counter and staging each row's 27
  *     pulled source rows (and, for the deviation storages, the 9 scale rows) in shared
@@ -229,6 +229,12 @@ elbm_status elbm_step(elbm_handle h, int64_t nsteps);
  * (values still written) if any population is NaN or infinite. */
 elbm_status elbm_reduce(elbm_handle h, double* mass, double* entropy, double* gmin,
                         int64_t* n_fallback);
+
+/* Deviation storages: node updates, since the last init, whose 16-bit deviations could not
+ * hold the node's shape (saturation, or a net mass far below the populations' magnitudes,
+ * detected as a mass correction sum_i 2^-e_i v_i of magnitude 1/2 or more) and that were
+ * stored as their equilibrium shape with their mass kept.  Always 0 for FP64 and FP32. */
+elbm_status elbm_storage_projections(elbm_handle h, int64_t* n);
 
 /* Steps taken since the last init. */
 elbm_status elbm_get_step(elbm_handle h, int64_t* step);

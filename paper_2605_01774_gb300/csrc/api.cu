@@ -121,6 +121,7 @@ void rebuild_consts(elbm_ctx* h) {
     const double P = poly_of(i, u);
     const double cu = cx_of(i) * u[0] + cy_of(i) * u[1] + cz_of(i) * u[2];
     k.E[i] = w_of(i) * P;
+    k.Ek[i] = std::ldexp(k.E[i], qexp_of(i));
     k.K3[i] = 3.0 * (1.0 / P - 1.0);
     k.L[i] = std::log(P) - 3.0 * cu + 1.5 * uu;
     k.M[i] = 1.0 / (w_of(i) * P);
@@ -141,6 +142,7 @@ void rebuild_consts(elbm_ctx* h) {
   PopConsts<float>& f = h->kf;
   for (int i = 0; i < Q; ++i) {
     f.E[i] = (float)k.E[i];
+    f.Ek[i] = (float)k.Ek[i];
     f.K3[i] = (float)k.K3[i];
     f.L[i] = (float)k.L[i];
     f.M[i] = (float)k.M[i];
@@ -398,6 +400,7 @@ static elbm_status write_state(elbm_handle h, const void* in, elbm_dtype dt, int
   CK(launch_write_state(S, dev, dt == ELBM_DTYPE_F32, from_phi, h->stream), "write state");
   if (tmp) CK(cudaFreeAsync(tmp, h->stream), "cudaFreeAsync");
   CK(cudaMemsetAsync(h->d_counters, 0, sizeof(unsigned long long), h->stream), "memset");
+  CK(cudaMemsetAsync(h->d_counters + 3, 0, sizeof(unsigned long long), h->stream), "memset");
   h->step = 0;
   h->initialized = true;
   return ELBM_OK;
@@ -545,6 +548,15 @@ elbm_status elbm_reduce(elbm_handle h, double* mass, double* entropy, double* gm
   if (n_fallback) *n_fallback = (int64_t)fb;
   if (check_timeout(h) != ELBM_OK) return ELBM_ERR_TIMEOUT;
   if (o[3] > 0) return fail(h, ELBM_ERR_NONFINITE, std::to_string((long long)o[3]) + " non-finite populations");
+  return ELBM_OK;
+}
+
+elbm_status elbm_storage_projections(elbm_handle h, int64_t* n) {
+  if (!h || !n) return fail(h, ELBM_ERR_ARG, "null argument");
+  unsigned long long c = 0;
+  CK(cudaMemcpyAsync(&c, h->d_counters + 3, sizeof(c), cudaMemcpyDeviceToHost, h->stream), "memcpy");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  *n = (int64_t)c;
   return ELBM_OK;
 }
 

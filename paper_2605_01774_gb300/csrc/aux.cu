@@ -72,7 +72,7 @@ k_write(Elem* __restrict__ pops, float* __restrict__ scale, Grid G, const void* 
       a[i] = R(2.0 * w_of(i)) * phw - v;
     }
   }
-  Storage<Elem>::store(pops, scale, G.N, n, a, k.E, R(NAN));
+  Storage<Elem>::store(pops, scale, G.N, n, a, k.Ek, R(NAN));
 }
 
 // ----------------------------------------------------------------- read state

@@ -23,6 +23,7 @@ namespace elbm {
 template <typename R>
 struct PopConsts {
   R E[Q];    // W_i P_i(u)
+  R Ek[Q];   // E_i 2^e_i (e_i = qexp_of(i)): the equilibrium shape in stored-deviation units
   R K3[Q];   // 3 (1/P_i(u) - 1)
   R L[Q];    // ln P_i(u) - 3 c_i.u + 1.5 u.u
   R M[Q];    // 1 / (W_i P_i(u))

@@ -22,7 +22,8 @@ struct StepLaunch {
   float* sout;
   const void* T6;               // per-node T = 2I - S [6][N] (double for FP64, else float) or null
   const float* src;             // per-node source [N] or null
-  unsigned long long* counters; // [0] fallback count, [2] staging wait ran out, [4..5] row tickets
+  unsigned long long* counters; // [0] fallback count, [2] staging wait ran out, [3] nodes stored
+                                // as their equilibrium shape, [4..5] row tickets
   const PopConsts<double>* kd;  // host copies, passed by value to the kernel
   const PopConsts<float>* kf;
   int variant;                  // 0 auto, 1 one thread per node with global gathers, 2 staged rows

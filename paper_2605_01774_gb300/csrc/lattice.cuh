@@ -15,6 +15,9 @@ __host__ __device__ constexpr int opp_of(int i) { return 26 - i; }
 __host__ __device__ constexpr int nnz_of(int i) {
   return (cx_of(i) != 0) + (cy_of(i) != 0) + (cz_of(i) != 0);
 }
+// Exponent e_i = 2 + 2 m (m = number of nonzero components of c_i) of the scaling of the
+// stored deviations: W_i 2^e_i = 32/27 for every i.
+__host__ __device__ constexpr int qexp_of(int i) { return 2 + 2 * nnz_of(i); }
 // W_i = (2/3)^(3-m) (1/6)^m: 8/27, 2/27, 1/54, 1/216 for m = 0..3
 __host__ __device__ constexpr double w_of(int i) {
   return nnz_of(i) == 0 ? 8.0 / 27.0 : nnz_of(i) == 1 ? 2.0 / 27.0 : nnz_of(i) == 2 ? 1.0 / 54.0 : 1.0 / 216.0;

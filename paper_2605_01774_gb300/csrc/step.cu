@@ -25,7 +25,7 @@ k_step(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
-  bool took = false;
+  bool took = false, proj = false;
   if (x < G.nx && y < G.ny) {
     const int n = x + G.nx * (y + G.ny * z);
     R g[Q];
@@ -44,10 +44,15 @@ k_step(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G
     } else {
       took = collide_node<R, VEL, ROOT>(g, T, k, fallback != 0, phi);
     }
-    Storage<Elem>::store(pout, sout, G.N, n, g, k.E, phi);
+    proj = Storage<Elem>::store(pout, sout, G.N, n, g, k.Ek, phi);
   }
-  const unsigned m = __ballot_sync(0xffffffffu, took);
-  if (m != 0u && ((threadIdx.y * blockDim.x + threadIdx.x) & 31) == 0) atomicAdd(counters, (unsigned long long)__popc(m));
+  // one counter update per block
+  const int c = __syncthreads_count(took);
+  if (c != 0 && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(counters, (unsigned long long)c);
+  if constexpr (Storage<Elem>::dev) {
+    const int p = __syncthreads_count(proj);
+    if (p != 0 && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(counters + 3, (unsigned long long)p);
+  }
 }
 
 static dim3 block_for(int nx) {
@@ -79,14 +84,9 @@ static cudaError_t launch_v(const StepLaunch& L, cudaStream_t s) {
 }
 
 cudaError_t launch_step(const StepLaunch& L, cudaStream_t s) {
-  // auto: the staged-row kernel for the 16-bit deviation storages (where it measured at
-  // least as fast), the per-node kernel for FP32 and FP64 (faster there)
-  const bool rows = L.variant == 2 || (L.variant == 0 && L.prec >= 2);
-  if (rows && rows_eligible(L.prec, L.nx)) {
-    const cudaError_t e = launch_step_rows(L, s);
-    if (e != cudaErrorNotSupported || L.variant == 2) return e;
-  }
-  if (L.variant == 2) return cudaErrorNotSupported;
+  // auto is the per-node kernel: on the advected-plume workload (issue-bound collision,
+  // positivity fallback at most nodes) it measured at least as fast for every storage
+  if (L.variant == 2) return rows_eligible(L.prec, L.nx) ? launch_step_rows(L, s) : cudaErrorNotSupported;
   switch (L.prec) {
     case 0: return launch_v<double>(L, s);
     case 1: return launch_v<float>(L, s);

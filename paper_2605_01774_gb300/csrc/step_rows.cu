@@ -83,7 +83,7 @@ __device__ __forceinline__ void staged_pull(R (&g)[Q], const unsigned char* stag
     for (int i = 0; i < Q; ++i) {
       const int xs = cx_of(i) == 1 ? xm : (cx_of(i) == -1 ? xp : x);
       const float s = S[(i % 9) * W + xs];
-      g[i] = s * fmaf(float(w_of(i)), Codec<Elem>::to_f(P[i * W + xs]), k.E[i]);
+      g[i] = s * fmaf(float(1.0 / (1 << qexp_of(i))), Codec<Elem>::to_f(P[i * W + xs]), k.E[i]);
     }
   } else {
 #pragma unroll
@@ -133,7 +133,8 @@ __device__ __forceinline__ int take_row(unsigned long long* counters, int nrows,
   return row;
 }
 
-// counters[0]: fallback nodes; [2]: set when a staging wait ran out; [TICKET]: rows handed
+// counters[0]: fallback nodes; [2]: set when a staging wait ran out; [3]: nodes stored as
+// their equilibrium shape (deviation storages, see Storage::store); [TICKET]: rows handed
 // out in this launch; [DONE]: blocks finished -- the last one resets both for the next launch.
 template <typename Elem, int VEL, bool ROOT>
 __global__ void __launch_bounds__(RT, rows_min_blocks<Elem>())
@@ -166,7 +167,7 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
     }
   }
   __syncthreads();
-  unsigned took = 0;
+  unsigned took = 0, proj = 0;
   int it = 0;
   for (;; ++it) {
     const int s = it % STAGES;
@@ -209,7 +210,7 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
           t = collide_node<R, VEL, ROOT>(g, T, k, fallback != 0, phi);
         }
         took += t ? 1u : 0u;
-        Storage<Elem>::store(pout, sout, (int)G.N, n, g, k.E, phi);
+        proj += Storage<Elem>::store(pout, sout, (int)G.N, n, g, k.Ek, phi) ? 1u : 0u;
       }
     }
     __syncthreads();
@@ -225,6 +226,11 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) took += __shfl_xor_sync(0xffffffffu, took, o);
   if (took != 0u && (threadIdx.x & 31) == 0) atomicAdd(counters, (unsigned long long)took);
+  if constexpr (Storage<Elem>::dev) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) proj += __shfl_xor_sync(0xffffffffu, proj, o);
+    if (proj != 0u && (threadIdx.x & 31) == 0) atomicAdd(counters + 3, (unsigned long long)proj);
+  }
   if (threadIdx.x == 0) {
     // every block has taken its last ticket before it counts itself done
     __threadfence();

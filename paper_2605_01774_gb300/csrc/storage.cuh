@@ -2,11 +2,15 @@
 //
 // Plain formats (FP64, FP32) keep the post-collision populations A_i(n) as they
 // are.  Deviation formats keep, per node, an FP32 scale phi_s(n) and 27 16-bit
-// relative deviations q_i(n) from the equilibrium shape of the (uniform)
-// velocity:  A_i(n) = phi_s(n) (E_i + W_i q_i(n)),  E_i = W_i P_i(u).
-// Encoding takes phi* = sum_i A_i, q_i = round((A_i / phi* - E_i) / W_i) and
-// phi_s = phi* / (1 + sum_i W_i q_i), so the stored node mass sum_i A_i equals
-// phi* up to FP32 rounding whatever the 16-bit rounding of the q_i was.
+// scaled relative deviations v_i(n) from the equilibrium shape of the (uniform)
+// velocity:  A_i(n) = phi_s(n) (E_i + 2^-e_i v_i(n)),  E_i = W_i P_i(u), with the
+// exponents e_i = 2 + 2 m_i of lattice.cuh (W_i 2^e_i = 32/27 for all i, so v_i is the
+// relative deviation (A_i/phi - E_i)/W_i times 32/27 and all 27 streams share one range).
+// Encoding takes phi* = sum_i A_i, v_i = round(A_i (2^e_i/phi*) - E_i 2^e_i) (one fused
+// multiply-add; exact scaling by 2^e_i commutes with the rounding), and
+// phi_s = phi* / (1 + sum_i 2^-e_i v_i), so the stored node mass sum_i A_i equals phi* up
+// to FP32 rounding whatever the 16-bit rounding of the v_i was.  FP16 conversion saturates
+// at +-65504 and keeps NaN (a non-finite state stays visible to the reductions).
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -23,7 +27,9 @@ template <>
 struct Codec<__half> {
   static __device__ __forceinline__ float to_f(__half h) { return __half2float(h); }
   static __device__ __forceinline__ __half from_f(float f) {
-    return __float2half_rn(fminf(fmaxf(f, -65504.f), 65504.f));
+    unsigned short h;
+    asm("cvt.rn.satfinite.f16.f32 %0, %1;" : "=h"(h) : "f"(f));
+    return __ushort_as_half(h);
   }
 };
 template <>
@@ -44,16 +50,20 @@ struct Storage {
     const Elem v = __ldg(pops + (i * N + src));  // 27 N < 2^31 is checked at creation
     if constexpr (dev) {
       const float s = __ldg(scale + src);
-      return s * fmaf(float(w_of(i)), Codec<Elem>::to_f(v), E_i);
+      return s * fmaf(float(1.0 / (1 << qexp_of(i))), Codec<Elem>::to_f(v), E_i);
     } else {
       return v;
     }
   }
 
-  // Write the 27 post-collision values of node n.  `mass` is sum_i a_i when the caller
-  // knows it exactly (a collision conserves the node's phi); pass NaN to have it summed.
-  static __device__ __forceinline__ void store(Elem* __restrict__ pops, float* __restrict__ scale, int N,
-                                               int n, const real (&a)[Q], const real (&E)[Q], real mass) {
+  // Write the 27 post-collision values of node n.  Ek = E_i 2^e_i.  `mass` is sum_i a_i
+  // when the caller knows it exactly (a collision conserves the node's phi); pass NaN to
+  // have it summed.  Returns true where a deviation storage could not hold the node's
+  // shape: when the 16-bit rounding moved the mass correction sum_i 2^-e_i v_i by 1/2 or
+  // more (saturated values, or a net mass far below the populations' magnitudes), the
+  // node is stored as its equilibrium shape with its mass kept (v = 0, phi_s = phi*).
+  static __device__ __forceinline__ bool store(Elem* __restrict__ pops, float* __restrict__ scale, int N,
+                                               int n, const real (&a)[Q], const real (&Ek)[Q], real mass) {
     if constexpr (dev) {
       float phi = mass;
       if (!(phi == phi)) {
@@ -63,23 +73,31 @@ struct Storage {
       }
       if (fabsf(phi) > 1e-30f) {
         const float inv = 1.0f / phi;
+        const float ik[4] = {4.f * inv, 16.f * inv, 64.f * inv, 256.f * inv};   // 2^e / phi
         float s = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-          const float r = fmaf(a[i], inv, -E[i]) * float(1.0 / w_of(i));
-          const Elem q = Codec<Elem>::from_f(r);
-          s = fmaf(float(w_of(i)), Codec<Elem>::to_f(q), s);
+          const Elem q = Codec<Elem>::from_f(fmaf(a[i], ik[nnz_of(i)], -Ek[i]));
+          s = fmaf(float(1.0 / (1 << qexp_of(i))), Codec<Elem>::to_f(q), s);
           pops[i * N + n] = q;
         }
-        scale[n] = phi / (1.0f + s);
-      } else {
+        if (!(fabsf(s) >= 0.5f)) {          // NaN stays on this path and stays visible
+          scale[n] = phi / (1.0f + s);
+          return false;
+        }
 #pragma unroll
         for (int i = 0; i < Q; ++i) pops[i * N + n] = Codec<Elem>::from_f(0.f);
         scale[n] = phi;
+        return true;
       }
+#pragma unroll
+      for (int i = 0; i < Q; ++i) pops[i * N + n] = Codec<Elem>::from_f(0.f);
+      scale[n] = phi;
+      return false;
     } else {
 #pragma unroll
       for (int i = 0; i < Q; ++i) pops[i * N + n] = a[i];
+      return false;
     }
   }
 };

@@ -66,6 +66,7 @@ def lib() -> C.CDLL:
         "elbm_set_source_amplitude": (S, [H, C.c_double]),
         "elbm_set_lambda_mode": (S, [H, C.c_int32]),
         "elbm_set_step_kernel": (S, [H, C.c_int32]),
+        "elbm_storage_projections": (S, [H, C.POINTER(C.c_int64)]),
         "elbm_step_source_schedule": (S, [H, D, I64]),
         "elbm_init_equilibrium": (S, [H, P, S]),
         "elbm_write_populations": (S, [H, P, S]),
@@ -211,6 +212,12 @@ def elbm_set_lambda_mode(h, mode):
 
 def elbm_set_step_kernel(h, variant):
     _check(lib().elbm_set_step_kernel(h, int(variant)), h)
+
+
+def elbm_storage_projections(h) -> int:
+    n = C.c_int64(0)
+    _check(lib().elbm_storage_projections(h, C.byref(n)), h)
+    return int(n.value)
 
 
 def elbm_set_source_amplitude(h, a):
