@@ -84,9 +84,14 @@ static cudaError_t launch_v(const StepLaunch& L, cudaStream_t s) {
 }
 
 cudaError_t launch_step(const StepLaunch& L, cudaStream_t s) {
-  // auto is the per-node kernel: on the advected-plume workload (issue-bound collision,
-  // positivity fallback at most nodes) it measured at least as fast for every storage
+  // auto: the staged-row kernel where its row length is compiled in (nx = 256 or 512,
+  // uniform velocity, closed-form stabilizer; measured faster for FP32 and the deviation
+  // storages on the 256^3 plume), else the per-node kernel
   if (L.variant == 2) return rows_eligible(L.prec, L.nx) ? launch_step_rows(L, s) : cudaErrorNotSupported;
+  const bool root = (L.prec == 0 ? L.kd->root : L.kf->root) != 0;
+  if (L.variant == 0 && L.prec != 0 && (L.nx == 256 || L.nx == 512) && L.vel != 2 && !root &&
+      rows_eligible(L.prec, L.nx))
+    return launch_step_rows(L, s);
   switch (L.prec) {
     case 0: return launch_v<double>(L, s);
     case 1: return launch_v<float>(L, s);

@@ -47,11 +47,12 @@ __host__ __device__ constexpr size_t stage_bytes(int W) {
 
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// Copies of one row, spread over the lanes of warp 0 (lane 0 posts the byte count first).
+// Copies of one row of length W, spread over the lanes of warp 0 (lane 0 posts the byte
+// count first).
 template <typename Elem>
-__device__ void issue_row(const Field<Elem>& in, const Grid& G, int row, unsigned char* stage, uint64_t* bar) {
+__device__ void issue_row(const Field<Elem>& in, const Grid& G, int W, int row, unsigned char* stage, uint64_t* bar) {
   const int lane = threadIdx.x & 31;
-  const int W = G.nx, Ny = G.ny, Nz = G.nz;
+  const int Ny = G.ny, Nz = G.nz;
   const int y = row % Ny, z = row / Ny;
   if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)stage_bytes<Elem>(W));
   __syncwarp();
@@ -133,10 +134,12 @@ __device__ __forceinline__ int take_row(unsigned long long* counters, int nrows,
   return row;
 }
 
+// WC > 0: the row length nx as a compile-time constant (shared-memory offsets become
+// immediates), else taken from G.
 // counters[0]: fallback nodes; [2]: set when a staging wait ran out; [3]: nodes stored as
 // their equilibrium shape (deviation storages, see Storage::store); [TICKET]: rows handed
 // out in this launch; [DONE]: blocks finished -- the last one resets both for the next launch.
-template <typename Elem, int VEL, bool ROOT>
+template <typename Elem, int VEL, bool ROOT, int WC>
 __global__ void __launch_bounds__(RT, rows_min_blocks<Elem>())
 k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G,
             const typename Storage<Elem>::real* __restrict__ T6, const float* __restrict__ src,
@@ -147,7 +150,7 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
   __shared__ uint64_t bars[STAGES];
   __shared__ int s_row[STAGES];
   __shared__ int abort_flag;
-  const int W = G.nx;
+  const int W = WC > 0 ? WC : G.nx;
   const size_t SB = stage_bytes<Elem>(W);
   const int nrows = G.ny * G.nz;
   const bool producer = threadIdx.x < 32;     // warp 0 takes the rows and issues their copies
@@ -163,7 +166,7 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
     for (int m = 0; m < STAGES - 1; ++m) {
       const int row = take_row(counters, nrows, exhausted);
       if (threadIdx.x == 0) s_row[m] = row;
-      if (row < nrows) issue_row(in, G, row, smem + m * SB, &bars[m]);
+      if (row < nrows) issue_row(in, G, W, row, smem + m * SB, &bars[m]);
     }
   }
   __syncthreads();
@@ -181,7 +184,7 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
       if (threadIdx.x == 0) s_row[sm] = nrow;
       if (nrow < nrows) {
         fence_proxy_async();
-        issue_row(in, G, nrow, smem + sm * SB, &bars[sm]);
+        issue_row(in, G, W, nrow, smem + sm * SB, &bars[sm]);
       }
     }
     if (!mbar_wait_bounded(&bars[s], (it / STAGES) & 1, WAIT_LIMIT)) {
@@ -243,9 +246,10 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
 
 namespace {
 
-// Blocks of k_step_rows<Elem, VEL, ROOT> resident per SM at row length W (0: not launchable);
-// raises the kernel's dynamic shared-memory limit as needed.  Cached per (device, W).
-template <typename Elem, int VEL, bool ROOT>
+// Blocks of k_step_rows<Elem, VEL, ROOT, WC> resident per SM at row length W (0: not
+// launchable); raises the kernel's dynamic shared-memory limit as needed.  Cached per
+// (device, W).
+template <typename Elem, int VEL, bool ROOT, int WC>
 int rows_occupancy(int W) {
   static int c_dev = -1, c_w = -1, c_nb = 0;
   int dev = 0;
@@ -253,9 +257,9 @@ int rows_occupancy(int W) {
   if (dev == c_dev && W == c_w) return c_nb;
   const size_t dyn = STAGES * stage_bytes<Elem>(W);
   int nb = 0;
-  if (cudaFuncSetAttribute(k_step_rows<Elem, VEL, ROOT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) ==
+  if (cudaFuncSetAttribute(k_step_rows<Elem, VEL, ROOT, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) ==
           cudaSuccess &&
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<Elem, VEL, ROOT>, RT, dyn) == cudaSuccess) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<Elem, VEL, ROOT, WC>, RT, dyn) == cudaSuccess) {
     c_dev = dev;
     c_w = W;
     c_nb = nb;
@@ -265,10 +269,10 @@ int rows_occupancy(int W) {
   return 0;
 }
 
-template <typename Elem, int VEL, bool ROOT>
+template <typename Elem, int VEL, bool ROOT, int WC>
 cudaError_t launch_rows_t(const StepLaunch& L, cudaStream_t s) {
   using R = typename Storage<Elem>::real;
-  const int nb = rows_occupancy<Elem, VEL, ROOT>(L.nx);
+  const int nb = rows_occupancy<Elem, VEL, ROOT, WC>(L.nx);
   if (nb <= 0) return cudaErrorNotSupported;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -279,7 +283,7 @@ cudaError_t launch_rows_t(const StepLaunch& L, cudaStream_t s) {
   Grid G{L.nx, L.ny, L.nz, L.N, L.dirichlet};
   const PopConsts<R>& k = *reinterpret_cast<const PopConsts<R>*>(std::is_same<R, double>::value ? (const void*)L.kd
                                                                                                : (const void*)L.kf);
-  k_step_rows<Elem, VEL, ROOT><<<grid, RT, STAGES * stage_bytes<Elem>(L.nx), s>>>(
+  k_step_rows<Elem, VEL, ROOT, WC><<<grid, RT, STAGES * stage_bytes<Elem>(L.nx), s>>>(
       in, static_cast<Elem*>(L.pout), L.sout, G, static_cast<const R*>(L.T6), L.src, L.u3, L.fallback, L.counters, k);
   return cudaGetLastError();
 }
@@ -287,9 +291,12 @@ cudaError_t launch_rows_t(const StepLaunch& L, cudaStream_t s) {
 template <typename Elem>
 cudaError_t launch_rows_v(const StepLaunch& L, cudaStream_t s) {
   const bool root = (std::is_same<Elem, double>::value ? L.kd->root : L.kf->root) != 0;
-  if (L.vel == 2) return root ? launch_rows_t<Elem, 2, true>(L, s) : launch_rows_t<Elem, 2, false>(L, s);
-  if (L.vel == 1) return root ? launch_rows_t<Elem, 1, true>(L, s) : launch_rows_t<Elem, 1, false>(L, s);
-  return launch_rows_t<Elem, 0, false>(L, s);
+  if (L.vel == 2) return root ? launch_rows_t<Elem, 2, true, 0>(L, s) : launch_rows_t<Elem, 2, false, 0>(L, s);
+  if (root) return L.vel == 1 ? launch_rows_t<Elem, 1, true, 0>(L, s) : launch_rows_t<Elem, 0, false, 0>(L, s);
+  // closed-form stabilizer, uniform velocity: row lengths 256 and 512 compiled in
+  if (L.nx == 256) return L.vel == 1 ? launch_rows_t<Elem, 1, false, 256>(L, s) : launch_rows_t<Elem, 0, false, 256>(L, s);
+  if (L.nx == 512) return L.vel == 1 ? launch_rows_t<Elem, 1, false, 512>(L, s) : launch_rows_t<Elem, 0, false, 512>(L, s);
+  return L.vel == 1 ? launch_rows_t<Elem, 1, false, 0>(L, s) : launch_rows_t<Elem, 0, false, 0>(L, s);
 }
 
 }  // namespace
