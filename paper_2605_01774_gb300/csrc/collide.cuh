@@ -178,7 +178,8 @@ __device__ __forceinline__ bool collide_node(R (&g)[Q], const Sym6<R>& T, const 
     R kappa = R(0);
     const R tiny = sizeof(R) == 4 ? R(1e-30) : R(1e-300);
     if (phi > tiny) {
-      const R inv = R(1) / phi;
+      // FP32: reciprocal-based quotients (2 ulp); inv only normalises the H-products
+      const R inv = sizeof(R) == 4 ? R(__fdividef(1.0f, float(phi))) : R(1) / phi;
       const Dots<R> cj(jx * inv, jy * inv, jz * inv);
       const Dots<R> ca(ax * inv, ay * inv, az * inv);
       R num = R(0), den = R(0);
@@ -190,7 +191,7 @@ __device__ __forceinline__ bool collide_node(R (&g)[Q], const Sym6<R>& T, const 
         den += dh * (dh * k.M[i]);
       }
       if (den > k.theta2) {
-        kappa = num / den;
+        kappa = sizeof(R) == 4 ? R(__fdividef(float(num), float(den))) : num / den;
         if constexpr (ROOT) {
           double geq[Q], dsp[Q], dhd[Q], L[Q];
           const Dots<R> cjd(jx, jy, jz), cad(ax, ay, az);

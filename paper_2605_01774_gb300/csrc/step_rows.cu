@@ -162,12 +162,16 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
   }
   __syncthreads();
   bool exhausted = false;
+  // thread 0: the ticket of the next row to issue, taken one iteration ahead so that the
+  // atomic's round trip overlaps a row of collisions instead of delaying warp 0
+  unsigned long long pend = 0;
   if (producer) {
     for (int m = 0; m < STAGES - 1; ++m) {
       const int row = take_row(counters, nrows, exhausted);
       if (threadIdx.x == 0) s_row[m] = row;
       if (row < nrows) issue_row(in, G, W, row, smem + m * SB, &bars[m]);
     }
+    if (!exhausted && threadIdx.x == 0) pend = atomicAdd(counters + TICKET, 1ull);
   }
   __syncthreads();
   unsigned took = 0, proj = 0;
@@ -180,12 +184,19 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
       // the buffer of iteration it + STAGES - 1 was last read in iteration it - 1, which
       // ended with a block barrier
       const int sm = (it + STAGES - 1) % STAGES;
-      const int nrow = take_row(counters, nrows, exhausted);
-      if (threadIdx.x == 0) s_row[sm] = nrow;
-      if (nrow < nrows) {
-        fence_proxy_async();
-        issue_row(in, G, W, nrow, smem + sm * SB, &bars[sm]);
+      int nrow = nrows;
+      if (!exhausted) {
+        const unsigned long long t = __shfl_sync(0xffffffffu, pend, 0);
+        if (t < (unsigned long long)nrows) {
+          nrow = (int)t;
+          if (threadIdx.x == 0) pend = atomicAdd(counters + TICKET, 1ull);
+        } else {
+          exhausted = true;
+        }
       }
+      if (threadIdx.x == 0) s_row[sm] = nrow;
+      // ordering of the previous reads of this buffer before the copies: the block barrier
+      if (nrow < nrows) issue_row(in, G, W, nrow, smem + sm * SB, &bars[sm]);
     }
     if (!mbar_wait_bounded(&bars[s], (it / STAGES) & 1, WAIT_LIMIT)) {
       abort_flag = 1;

@@ -72,7 +72,8 @@ struct Storage {
         for (int i = 0; i < Q; ++i) phi += a[i];
       }
       if (fabsf(phi) > 1e-30f) {
-        const float inv = 1.0f / phi;
+        // the encode's rounding is compensated exactly by phi_s, so 2-ulp reciprocal suffices
+        const float inv = __fdividef(1.0f, phi);
         const float ik[4] = {4.f * inv, 16.f * inv, 64.f * inv, 256.f * inv};   // 2^e / phi
         float s = 0.f;
 #pragma unroll
