@@ -128,7 +128,7 @@ elbm_status elbm_set_lambda_mode(elbm_handle h, int32_t mode);
 /* Which implementation of the fused collide-stream step (Eq. method-lbe with the collision
  * of Eqs. method-split..method-fallback) elbm_step launches; all give the same result up to
  * the order of floating-point operations, which is identical (bit-equal outputs).
- *   0 (default) auto: 2 for FP32 and the deviation storages where nx is 256 or 512 with a
+ *   0 (default) auto: 2 for FP32 and BF16 deviations where nx is 256 or 512 with a
  *     uniform velocity and the closed-form stabilizer (row length compiled in; measured
  *     faster there on the 256^3 advected plume), else 1.
  *   1 one thread per node gathering its 27 pulled populations from global memory.
@@ -141,6 +141,10 @@ elbm_status elbm_set_lambda_mode(elbm_handle h, int32_t mode);
  * A bounded staging wait that gives up makes the next elbm_synchronize or elbm_reduce
  * return ELBM_ERR_TIMEOUT. */
 elbm_status elbm_set_step_kernel(elbm_handle h, int32_t variant);
+
+/* The implementation (1 or 2, as above) elbm_step launches with the handle's current
+ * storage, size, velocity, stabilizer mode and elbm_set_step_kernel choice. */
+elbm_status elbm_get_step_kernel(elbm_handle h, int32_t* variant);
 
 /* --------------------------------------------------------- problem data */
 

@@ -492,6 +492,13 @@ elbm_status elbm_set_step_kernel(elbm_handle h, int32_t variant) {
   return ELBM_OK;
 }
 
+elbm_status elbm_get_step_kernel(elbm_handle h, int32_t* variant) {
+  if (!h || !variant) return fail(h, ELBM_ERR_ARG, "null argument");
+  const int vel = h->u3 ? 2 : ((h->u[0] != 0.0 || h->u[1] != 0.0 || h->u[2] != 0.0) ? 1 : 0);
+  *variant = step_variant(h->prec, h->nx, vel, h->lambda_mode != 0, h->step_kernel);
+  return ELBM_OK;
+}
+
 // A staging wait of the step kernel gave up (counters[2]); clears the flag.
 static elbm_status check_timeout(elbm_ctx* h) {
   unsigned long long t = 0;

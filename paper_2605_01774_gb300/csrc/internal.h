@@ -29,6 +29,9 @@ struct StepLaunch {
   int variant;                  // 0 auto, 1 one thread per node with global gathers, 2 staged rows
 };
 cudaError_t launch_step(const StepLaunch& L, cudaStream_t s);
+// The implementation launch_step runs (1 per-node, 2 staged rows) for a requested variant
+// (0 = auto).
+int step_variant(int prec, int nx, int vel, bool root, int requested);
 // Staged-row kernel (step_rows.cu): usable when rows_eligible(prec, nx); else cudaErrorNotSupported.
 bool rows_eligible(int prec, int nx);
 cudaError_t launch_step_rows(const StepLaunch& L, cudaStream_t s);

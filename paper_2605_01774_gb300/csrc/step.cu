@@ -83,15 +83,21 @@ static cudaError_t launch_v(const StepLaunch& L, cudaStream_t s) {
   return launch_t<Elem, 0, false>(L, s);
 }
 
-cudaError_t launch_step(const StepLaunch& L, cudaStream_t s) {
+int step_variant(int prec, int nx, int vel, bool root, int requested) {
+  if (requested != 0) return requested;
   // auto: the staged-row kernel where its row length is compiled in (nx = 256 or 512,
-  // uniform velocity, closed-form stabilizer; measured faster for FP32 and the deviation
-  // storages on the 256^3 plume), else the per-node kernel
-  if (L.variant == 2) return rows_eligible(L.prec, L.nx) ? launch_step_rows(L, s) : cudaErrorNotSupported;
+  // uniform velocity, closed-form stabilizer) for FP32 and BF16 deviations, which it
+  // steps faster on the 256^3 plume (FP32 by 8%, BF16 by 2%); else the per-node kernel
+  // (faster by 0.3% for FP16 deviations, equal for FP64)
+  if ((prec == 1 || prec == 3) && (nx == 256 || nx == 512) && vel != 2 && !root && rows_eligible(prec, nx))
+    return 2;
+  return 1;
+}
+
+cudaError_t launch_step(const StepLaunch& L, cudaStream_t s) {
   const bool root = (L.prec == 0 ? L.kd->root : L.kf->root) != 0;
-  if (L.variant == 0 && L.prec != 0 && (L.nx == 256 || L.nx == 512) && L.vel != 2 && !root &&
-      rows_eligible(L.prec, L.nx))
-    return launch_step_rows(L, s);
+  if (step_variant(L.prec, L.nx, L.vel, root, L.variant) == 2)
+    return rows_eligible(L.prec, L.nx) ? launch_step_rows(L, s) : cudaErrorNotSupported;
   switch (L.prec) {
     case 0: return launch_v<double>(L, s);
     case 1: return launch_v<float>(L, s);

@@ -66,6 +66,7 @@ def lib() -> C.CDLL:
         "elbm_set_source_amplitude": (S, [H, C.c_double]),
         "elbm_set_lambda_mode": (S, [H, C.c_int32]),
         "elbm_set_step_kernel": (S, [H, C.c_int32]),
+        "elbm_get_step_kernel": (S, [H, C.POINTER(C.c_int32)]),
         "elbm_storage_projections": (S, [H, C.POINTER(C.c_int64)]),
         "elbm_step_source_schedule": (S, [H, D, I64]),
         "elbm_init_equilibrium": (S, [H, P, S]),
@@ -212,6 +213,12 @@ def elbm_set_lambda_mode(h, mode):
 
 def elbm_set_step_kernel(h, variant):
     _check(lib().elbm_set_step_kernel(h, int(variant)), h)
+
+
+def elbm_get_step_kernel(h) -> int:
+    v = C.c_int32(0)
+    _check(lib().elbm_get_step_kernel(h, C.byref(v)), h)
+    return int(v.value)
 
 
 def elbm_storage_projections(h) -> int:
