@@ -39,6 +39,7 @@ import synth  # noqa: E402
 METRIC = "ELBM-ADE MLUPS & % HBM roofline, chosen vs plain form at stated L2 error"
 UNIT = "MLUPS"
 KERNEL_NAME = {1: "k_step", 2: "k_step_rows"}
+F64_FLOPS_PER_NODE = 706   # mean of the two launches in profiles/k_step_fp64_plume128_flops.md
 BYTES_PER_NODE = {"f64": 27 * 8 * 2, "f32": 27 * 4 * 2, "f16dev": (27 * 2 + 4) * 2, "bf16dev": (27 * 2 + 4) * 2}
 WORKLOAD = ("advected anisotropic Gaussian plume 256^3 periodic, u=(0.05,0.03,0.02), "
             "D=R diag(0.1,1e-3,1e-5) R^T (seeded ZYZ, seed 2), sigma0=8")
@@ -240,6 +241,15 @@ def run_ours(args, rank, world, local, dist):
     ms = max_over_ranks(ms, dist, dev)
     forms["f64"] = dict(ms_per_step=ms / k64, mlups=world * N * k64 / (ms * 1e-3) / 1e6,
                         bytes_per_node=BYTES_PER_NODE["f64"], steps=k64, n_fallback=d["n_fallback"])
+    # FP64 is bound by FP64 FMA throughput on this part: its arithmetic roofline against the
+    # measured FMA peak, with the per-node flop count from the committed ncu summary
+    peak64 = E.elbm_fma_peak("f64")
+    achieved64 = F64_FLOPS_PER_NODE * forms["f64"]["mlups"] * 1e6 / world
+    forms["f64"]["alu_roofline"] = {"bound": "alu", "unit": "TFLOP/s", "peak": peak64 / 1e12,
+                                    "achieved": achieved64 / 1e12, "frac": achieved64 / peak64,
+                                    "flops_per_node": F64_FLOPS_PER_NODE,
+                                    "source": "peak: elbm_fma_peak (measured now); flops per node: "
+                                              "profiles/k_step_fp64_plume128_flops.md"}
 
     # accuracy: phi after `ek` steps of each form vs the FP64 form (parity-tested against the oracle)
     ek = args.err_steps

@@ -304,6 +304,14 @@ elbm_status elbm_check_velocity(const double u[3]);
 /* T = 2I - S (6 doubles) of an SPD D6, computed in FP64 on the host. */
 elbm_status elbm_relaxation_complement(const double D6[6], double T6_out[6]);
 
+/* Measured fused multiply-add throughput of the CUDA cores of the current device, in
+ * flop/s (an FMA counts 2), for precision ELBM_F64 or ELBM_F32: many independent FMA
+ * chains per thread over several waves of blocks, best of five timed launches.  It is the
+ * arithmetic roofline of the FP64 step, which FP64 FMA issue bounds on this part.  The
+ * paper has no counterpart.  ELBM_ERR_ARG for other precisions or a null pointer,
+ * ELBM_ERR_CUDA on a runtime error.  Takes a few milliseconds; synchronises. */
+elbm_status elbm_fma_peak(int32_t precision, double* flops_per_s);
+
 #ifdef __cplusplus
 }
 #endif

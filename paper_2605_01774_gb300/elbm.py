@@ -85,6 +85,7 @@ def lib() -> C.CDLL:
         "elbm_check_tensor": (S, [D]),
         "elbm_check_velocity": (S, [D]),
         "elbm_relaxation_complement": (S, [D, D]),
+        "elbm_fma_peak": (S, [C.c_int32, C.POINTER(C.c_double)]),
     }
     I32, PI32, PI64 = C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64)
     sig.update({
@@ -481,3 +482,10 @@ class Lattice:
 
     def __exit__(self, *a):
         self.close()
+
+
+def elbm_fma_peak(prec="f64") -> float:
+    """CUDA-core FMA throughput of the current device in flop/s ("f64" or "f32")."""
+    v = C.c_double(0.0)
+    _check(lib().elbm_fma_peak(PRECISIONS[prec], C.byref(v)))
+    return float(v.value)
