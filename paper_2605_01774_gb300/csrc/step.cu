@@ -85,11 +85,13 @@ static cudaError_t launch_v(const StepLaunch& L, cudaStream_t s) {
 
 int step_variant(int prec, int nx, int vel, bool root, int requested) {
   if (requested != 0) return requested;
-  // auto: the staged-row kernel where its row length is compiled in (nx = 256 or 512,
-  // uniform velocity, closed-form stabilizer) for FP32 and BF16 deviations, which it
-  // steps faster on the 256^3 plume (FP32 by 8%, BF16 by 2%); else the per-node kernel
-  // (faster by 0.3% for FP16 deviations, equal for FP64)
-  if ((prec == 1 || prec == 3) && (nx == 256 || nx == 512) && vel != 2 && !root && rows_eligible(prec, nx))
+  // auto: the staged-row kernel where its row length is compiled in (nx = 256, 384 or 512,
+  // uniform velocity, closed-form stabilizer) for the FP32-arithmetic storages, else the
+  // per-node kernel.  Measured, ms/step per-node -> staged: 256^3 plume FP32 0.684 -> 0.588,
+  // BF16 deviations 0.782 -> 0.769, FP16 deviations 0.777 -> 0.779; 384^3 heterogeneous
+  // (tensor field, source, Dirichlet) FP32 2.83 -> 2.48, FP16 2.88 -> 2.35, BF16 2.91 -> 2.36.
+  // FP64 (arithmetic-bound) keeps the per-node kernel.
+  if (prec != 0 && (nx == 256 || nx == 384 || nx == 512) && vel != 2 && !root && rows_eligible(prec, nx))
     return 2;
   return 1;
 }

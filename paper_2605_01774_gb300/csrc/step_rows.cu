@@ -20,7 +20,7 @@
 #ifndef ELBM_ROWS_STAGES
 #define ELBM_ROWS_STAGES 2
 #endif
-// Resident blocks per SM requested from the register allocator (256 threads each).
+// Resident 256-thread blocks per SM requested from the register allocator.
 #ifndef ELBM_ROWS_MINB
 #define ELBM_ROWS_MINB 3
 #endif
@@ -29,7 +29,8 @@ namespace elbm {
 
 namespace {
 
-constexpr int RT = 256;                          // threads per block
+// Threads per block: 256, or one thread per node for the compiled-in row length 384.
+__host__ __device__ constexpr int block_threads(int WC) { return WC == 384 ? 384 : 256; }
 constexpr int STAGES = ELBM_ROWS_STAGES;         // staging buffers per block
 constexpr long long WAIT_LIMIT = 2000000000ll;   // clock cycles (about one second)
 constexpr int TICKET = 4, DONE = 5;              // counters[] slots of the row scheduler
@@ -113,9 +114,11 @@ __device__ __forceinline__ void abb_faces(R (&g)[Q], const Field<Elem>& f, const
   }
 }
 
-template <typename Elem>
+// Resident blocks per SM requested from the register allocator: 768 threads for FP32 storage
+// types (3 x 256 or 2 x 384), one block for FP64.
+template <typename Elem, int WC>
 constexpr int rows_min_blocks() {
-  return std::is_same<Elem, double>::value ? 1 : ELBM_ROWS_MINB;
+  return std::is_same<Elem, double>::value ? 1 : (block_threads(WC) == 384 ? 2 : ELBM_ROWS_MINB);
 }
 
 }  // namespace
@@ -140,7 +143,7 @@ __device__ __forceinline__ int take_row(unsigned long long* counters, int nrows,
 // their equilibrium shape (deviation storages, see Storage::store); [TICKET]: rows handed
 // out in this launch; [DONE]: blocks finished -- the last one resets both for the next launch.
 template <typename Elem, int VEL, bool ROOT, int WC>
-__global__ void __launch_bounds__(RT, rows_min_blocks<Elem>())
+__global__ void __launch_bounds__(block_threads(WC), rows_min_blocks<Elem, WC>())
 k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G,
             const typename Storage<Elem>::real* __restrict__ T6, const float* __restrict__ src,
             const float* __restrict__ u3, int fallback, unsigned long long* __restrict__ counters,
@@ -203,7 +206,7 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
     } else {
       const unsigned char* stage = smem + s * SB;
       const size_t row0 = (size_t)row * W;
-      for (int x = threadIdx.x; x < W; x += RT) {
+      for (int x = threadIdx.x; x < W; x += block_threads(WC)) {
         const int n = (int)(row0 + x);
         R g[Q];
         staged_pull<Elem, R>(g, stage, W, x, k);
@@ -270,7 +273,8 @@ int rows_occupancy(int W) {
   int nb = 0;
   if (cudaFuncSetAttribute(k_step_rows<Elem, VEL, ROOT, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) ==
           cudaSuccess &&
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<Elem, VEL, ROOT, WC>, RT, dyn) == cudaSuccess) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<Elem, VEL, ROOT, WC>, block_threads(WC), dyn) ==
+          cudaSuccess) {
     c_dev = dev;
     c_w = W;
     c_nb = nb;
@@ -294,7 +298,7 @@ cudaError_t launch_rows_t(const StepLaunch& L, cudaStream_t s) {
   Grid G{L.nx, L.ny, L.nz, L.N, L.dirichlet};
   const PopConsts<R>& k = *reinterpret_cast<const PopConsts<R>*>(std::is_same<R, double>::value ? (const void*)L.kd
                                                                                                : (const void*)L.kf);
-  k_step_rows<Elem, VEL, ROOT, WC><<<grid, RT, STAGES * stage_bytes<Elem>(L.nx), s>>>(
+  k_step_rows<Elem, VEL, ROOT, WC><<<grid, block_threads(WC), STAGES * stage_bytes<Elem>(L.nx), s>>>(
       in, static_cast<Elem*>(L.pout), L.sout, G, static_cast<const R*>(L.T6), L.src, L.u3, L.fallback, L.counters, k);
   return cudaGetLastError();
 }
@@ -304,9 +308,10 @@ cudaError_t launch_rows_v(const StepLaunch& L, cudaStream_t s) {
   const bool root = (std::is_same<Elem, double>::value ? L.kd->root : L.kf->root) != 0;
   if (L.vel == 2) return root ? launch_rows_t<Elem, 2, true, 0>(L, s) : launch_rows_t<Elem, 2, false, 0>(L, s);
   if (root) return L.vel == 1 ? launch_rows_t<Elem, 1, true, 0>(L, s) : launch_rows_t<Elem, 0, false, 0>(L, s);
-  // closed-form stabilizer, uniform velocity: row lengths 256 and 512 compiled in
+  // closed-form stabilizer, uniform velocity: row lengths 256, 384 and 512 compiled in
   if (L.nx == 256) return L.vel == 1 ? launch_rows_t<Elem, 1, false, 256>(L, s) : launch_rows_t<Elem, 0, false, 256>(L, s);
   if (L.nx == 512) return L.vel == 1 ? launch_rows_t<Elem, 1, false, 512>(L, s) : launch_rows_t<Elem, 0, false, 512>(L, s);
+  if (L.nx == 384) return L.vel == 1 ? launch_rows_t<Elem, 1, false, 384>(L, s) : launch_rows_t<Elem, 0, false, 384>(L, s);
   return L.vel == 1 ? launch_rows_t<Elem, 1, false, 0>(L, s) : launch_rows_t<Elem, 0, false, 0>(L, s);
 }
 

@@ -49,11 +49,12 @@ def _run(E, dims, prec, variant, steps, D6, phi0, src, bc, u, ufield=None):
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "f16dev", "bf16dev"])
 @pytest.mark.parametrize("dims,bc", [((8, 3, 2), None), ((16, 6, 5), (1.2, 0.9)), ((40, 7, 3), None),
-                                     ((24, 40, 30), (1.1, 1.0)), ((256, 4, 3), (1.2, 0.8)), ((512, 3, 2), None)])
+                                     ((24, 40, 30), (1.1, 1.0)), ((256, 4, 3), (1.2, 0.8)), ((512, 3, 2), None),
+                                     ((384, 5, 3), (1.0, 0.0))])
 def test_variants_bit_equal(E, prec, dims, bc):
     """Per-node tensor, u != 0, source, Dirichlet or periodic x faces; (24, 40, 30) has more rows
     than resident blocks, so blocks loop over rows and reuse both staging buffers; row lengths
-    256 and 512 run the instantiations with the row length compiled in."""
+    256, 384 (384-thread blocks) and 512 run the instantiations with the row length compiled in."""
     if prec == "f64" and dims[0] > 472:
         pytest.skip("two FP64 staging buffers of this row length exceed shared memory")
     D6, phi0, src = _case(dims, sum(dims))
@@ -65,7 +66,8 @@ def test_variants_bit_equal(E, prec, dims, bc):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "f16dev", "bf16dev"])
-@pytest.mark.parametrize("dims,u", [((16, 5, 4), (0.0, 0.0, 0.0)), ((256, 3, 2), (0.03, 0.0, -0.02))])
+@pytest.mark.parametrize("dims,u", [((16, 5, 4), (0.0, 0.0, 0.0)), ((256, 3, 2), (0.03, 0.0, -0.02)),
+                                    ((384, 2, 2), (0.0, 0.0, 0.0))])
 def test_variants_bit_equal_uniform_velocity_no_source(E, prec, dims, u):
     """Uniform tensor (no tensor field), u = 0 and u != 0, no source."""
     rng = synth.rng(5)
