@@ -206,12 +206,35 @@ def run_ours(args, rank, world, local, dist):
         ms = ev0.elapsed_time(ev1)
         return ms, (sampler.summary() if sampler else None)
 
+    if args.only and args.workload == "heterogeneous":
+        # the 384^3 two-phase porous workload (per-node tensor field, Gaussian source, Dirichlet
+        # x faces, u = 0): a parity-test configuration, timed here for one form
+        hw = synth.heterogeneous(n=args.size if args.size != 256 else 384)
+        Nh = int(np.prod(hw.dims))
+        lat = E.Lattice(hw.dims, args.only, bc=hw.dirichlet_x, stream=stream)
+        E.elbm_set_tensor_field(lat.h, torch.as_tensor(hw.D6_field, dtype=torch.float32, device=dev))
+        E.elbm_set_source(lat.h, torch.as_tensor(hw.source, dtype=torch.float32, device=dev))
+        E.elbm_set_params(lat.h, theta=THETA)
+        E.elbm_set_step_kernel(lat.h, args.step_kernel)
+        stream.wait_stream(torch.cuda.current_stream(dev))
+        E.elbm_init_equilibrium(lat.h, torch.as_tensor(hw.phi0, dtype=torch.float32, device=dev))
+        ms, _ = timed(lat, args.steps, args.warmup)
+        kern = KERNEL_NAME[E.elbm_get_step_kernel(lat.h)]
+        lat.close()
+        # + tensor field (6 values in the arithmetic type) and the FP32 source plane
+        bpn = BYTES_PER_NODE[args.only] + (48 if args.only == "f64" else 24) + 4
+        peak, _ = measured_peaks()
+        return {"only": args.only, "workload": "heterogeneous", "nodes": Nh, "kernel": kern,
+                "ms_per_step": ms / args.steps, "mlups": Nh * args.steps / (ms * 1e-3) / 1e6,
+                "bytes_per_node": bpn, "hbm_frac_of_measured": bpn * Nh / (ms / args.steps * 1e-3) / 1e9 / peak}
+
     if args.only:
         # one form, timing only (the command profiled by ncu)
         lat = make(args.only)
         ms, _ = timed(lat, args.steps, args.warmup)
+        kern = KERNEL_NAME[E.elbm_get_step_kernel(lat.h)]
         lat.close()
-        return {"only": args.only, "nodes": N, "ms_per_step": ms / args.steps,
+        return {"only": args.only, "nodes": N, "kernel": kern, "ms_per_step": ms / args.steps,
                 "mlups": N * args.steps / (ms * 1e-3) / 1e6}
 
     forms = {}
@@ -444,6 +467,8 @@ def main():
                     help="steps per mode of the 512-domain sweep (0 skips it)")
     ap.add_argument("--step-kernel", type=int, default=0, choices=[0, 1, 2],
                     help="step implementation: 0 auto, 1 per-node gathers, 2 staged rows")
+    ap.add_argument("--workload", default="plume", choices=["plume", "heterogeneous"],
+                    help="with --only: time the 256^3 plume (default) or the 384^3 heterogeneous workload")
     ap.add_argument("--only", default=None, choices=["f16dev", "bf16dev", "f32", "f64"],
                     help="time one form only (profiling runs)")
     args = ap.parse_args()
