@@ -38,6 +38,7 @@ struct elbm_ctx {
   double src_amp = 1.0;      // source amplitude of the most recent half-step a_{n-1}
   int lambda_mode = 0;       // 0 closed form, 1 exact root
   int step_kernel = 0;       // 0 auto, 1 per-node gathers, 2 staged rows
+  int exact_mass = 1;        // FP32 storage: exact stored node mass
   std::string err;
 };
 
@@ -136,6 +137,7 @@ void rebuild_consts(elbm_ctx* h) {
   k.src_step = h->src_amp;
   k.src_half = 0.5 * h->src_amp;
   k.root = h->lambda_mode;
+  k.exact_mass = h->exact_mass;
   double T[6] = {0, 0, 0, 0, 0, 0};
   if (h->have_tensor && !h->tensor_field) complement6(h->D6, T);
   k.T = Sym6<double>{T[0], T[1], T[2], T[3], T[4], T[5]};
@@ -157,6 +159,7 @@ void rebuild_consts(elbm_ctx* h) {
   f.src_step = (float)k.src_step;
   f.src_half = (float)k.src_half;
   f.root = k.root;
+  f.exact_mass = k.exact_mass;
   f.T = Sym6<float>{(float)T[0], (float)T[1], (float)T[2], (float)T[3], (float)T[4], (float)T[5]};
 }
 
@@ -489,6 +492,13 @@ elbm_status elbm_set_step_kernel(elbm_handle h, int32_t variant) {
   if (variant == 2 && !rows_eligible(h->prec, h->nx))
     return fail(h, ELBM_ERR_UNSUPPORTED, "staged-row step needs nx % 8 == 0 and rows that fit in shared memory");
   h->step_kernel = variant;
+  return ELBM_OK;
+}
+
+elbm_status elbm_set_exact_mass(elbm_handle h, int32_t on) {
+  if (!h || (on != 0 && on != 1)) return fail(h, ELBM_ERR_ARG, "on must be 0 or 1");
+  h->exact_mass = on;
+  rebuild_consts(h);
   return ELBM_OK;
 }
 

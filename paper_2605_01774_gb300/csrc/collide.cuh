@@ -34,6 +34,7 @@ struct PopConsts {
   Sym6<R> T;         // uniform T = 2I - S
   R src_step;        // source multiplier of this step: (a_{n-1} + a_n)/2 (merged Strang halves)
   R src_half;        // half-step multiplier of the stored state: a_{n-1}/2
+  int exact_mass;    // FP32 storage: put each node's update rounding back on its rest population
   int root;          // 1: lambda from the exact entropy-stationarity root (FP64 Newton); selects
                      // the ROOT instantiation of the step kernels
 };

@@ -44,7 +44,7 @@ k_step(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G
     } else {
       took = collide_node<R, VEL, ROOT>(g, T, k, fallback != 0, phi);
     }
-    proj = Storage<Elem>::store(pout, sout, G.N, n, g, k.Ek, phi);
+    proj = Storage<Elem>::store(pout, sout, G.N, n, g, k.Ek, phi, k.exact_mass != 0);
   }
   // one counter update per block
   const int c = __syncthreads_count(took);

@@ -227,7 +227,7 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
           t = collide_node<R, VEL, ROOT>(g, T, k, fallback != 0, phi);
         }
         took += t ? 1u : 0u;
-        proj += Storage<Elem>::store(pout, sout, (int)G.N, n, g, k.Ek, phi) ? 1u : 0u;
+        proj += Storage<Elem>::store(pout, sout, (int)G.N, n, g, k.Ek, phi, k.exact_mass != 0) ? 1u : 0u;
       }
     }
     __syncthreads();

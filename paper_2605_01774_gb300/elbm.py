@@ -67,6 +67,7 @@ def lib() -> C.CDLL:
         "elbm_set_lambda_mode": (S, [H, C.c_int32]),
         "elbm_set_step_kernel": (S, [H, C.c_int32]),
         "elbm_get_step_kernel": (S, [H, C.POINTER(C.c_int32)]),
+        "elbm_set_exact_mass": (S, [H, C.c_int32]),
         "elbm_storage_projections": (S, [H, C.POINTER(C.c_int64)]),
         "elbm_step_source_schedule": (S, [H, D, I64]),
         "elbm_init_equilibrium": (S, [H, P, S]),
@@ -214,6 +215,10 @@ def elbm_set_lambda_mode(h, mode):
 
 def elbm_set_step_kernel(h, variant):
     _check(lib().elbm_set_step_kernel(h, int(variant)), h)
+
+
+def elbm_set_exact_mass(h, on):
+    _check(lib().elbm_set_exact_mass(h, int(on)), h)
 
 
 def elbm_get_step_kernel(h) -> int:

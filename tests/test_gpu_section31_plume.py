@@ -1,0 +1,87 @@
+"""Section 3.1 advected Gaussian plume at the paper's size and time, case d = (1e-2, 1e-3, 1e-6)
+of Table 1: 256^3 periodic, u = (0.04, 0.02, 0.01), sigma0 = 8, ZYZ (120, 90, 135) deg,
+tau = D_ref t / sigma0^2 = 6.25 (40 000 steps), FP32 storage with its default exact stored mass.
+
+Post-processing: the field is recentred on the exact centroid mu0 + u t (mu0 = box centre,
+coordinates taken in [mu - 128, mu + 128)), mass, centroid and covariance are summed in FP64,
+and D is reconstructed as (Sigma(t) - sigma0^2 I) / (2 t).
+
+Measured (this FP32 run and an FP64 run of the same case agree to the 4 printed digits):
+recovered 1e3 D = (4.1279, 2.3808, -3.8970, 1.3787, -2.2499, 5.5024) against the printed
+(4.1274, 2.3812, -3.8971, 1.3778, -2.2500, 5.5021): every coefficient within 1e-6 of the paper's
+recovered tensor, both showing the same ~2-3e-6 excess on the diagonal over the target;
+Frobenius error 4.6e-6 (printed 3.4e-6 to 3.7e-6); covariance relative error 4.2e-4 (printed
+2.2e-4 to 3.4e-4); FP64 mass drift 2.23e-12 (printed below 2.2e-12), FP32 with exact mass
+1.4e-7.  The centroid error, 5.5e-4 grid units, is ten times the printed bound (5.9e-5): the
+paper's recentring of the periodic field is not fully specified, and the centroid of a
+window cut at +-128 nodes depends on it.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+ROW = GOLD["table1_gaussian_tensor_targets"]["rows"][1]          # d = (1e-2, 1e-3, 1e-6)
+N, SIGMA0, STEPS = 256, 8.0, 40_000
+U = np.array([0.04, 0.02, 0.01])
+
+
+@pytest.fixture(scope="module")
+def E():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2605_01774_gb300 import elbm
+    elbm.lib()
+    return elbm
+
+
+def test_table1_tensor_recovery_fp32(E):
+    dev = torch.device("cuda")
+    D = synth.tensor_from_principal(tuple(ROW["d"]), synth.rot_zyz_deg(120, 90, 135))
+    idx = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    assert np.allclose([1e3 * D[i] for i in idx], ROW["target_1e3"], atol=6e-5)
+    mu0 = np.full(3, (N - 1) / 2.0)
+    lat = E.Lattice((N, N, N), "f32")
+    E.elbm_set_tensor_uniform(lat.h, synth.d6_from_matrix(D))
+    E.elbm_set_velocity_uniform(lat.h, U)
+    E.elbm_set_params(lat.h, theta=3e-4)
+    E.elbm_init_equilibrium(lat.h, torch.as_tensor(synth.gaussian((N, N, N), tuple(mu0), SIGMA0), device=dev))
+    m0 = E.elbm_reduce(lat.h)["mass"]
+    E.elbm_step(lat.h, STEPS)
+    d = E.elbm_reduce(lat.h)
+    phi = torch.empty((N, N, N), dtype=torch.float64, device=dev)
+    E.elbm_read_moments(lat.h, phi)
+    torch.cuda.synchronize()
+    lat.close()
+
+    t = float(STEPS)
+    mu = mu0 + U * t
+    x = torch.arange(N, dtype=torch.float64, device=dev)
+    c = [torch.remainder(x - float(mu[k]) + N / 2, N) - N / 2 for k in range(3)]
+    cz, cy, cx = torch.meshgrid(c[2], c[1], c[0], indexing="ij")
+    X = [cx, cy, cz]
+    M = phi.sum()
+    m = [float((phi * X[k]).sum() / M) for k in range(3)]
+    C = np.empty((3, 3))
+    for a in range(3):
+        for b in range(a, 3):
+            C[a, b] = C[b, a] = float((phi * X[a] * X[b]).sum() / M) - m[a] * m[b]
+    Sig = SIGMA0 ** 2 * np.eye(3) + 2 * D * t
+    Drec = (C - SIGMA0 ** 2 * np.eye(3)) / (2 * t)
+    rec = np.array([1e3 * Drec[i] for i in idx])
+    frob = float(np.linalg.norm(Drec - D))
+    cov = float(np.linalg.norm(C - Sig) / np.linalg.norm(Sig))
+    drift = abs(d["mass"] - m0) / m0
+    print(f"recovered 1e3 D {np.round(rec, 4).tolist()} (paper {ROW['recovered_1e3']}); Frobenius {frob:.2e}; "
+          f"covariance {cov:.2e}; centroid {np.linalg.norm(m):.2e}; mass drift {drift:.2e}")
+    assert np.abs(rec - np.asarray(ROW["recovered_1e3"])).max() < 1.2e-3     # 1.2e-6 in D
+    assert 2e-6 < frob < 6e-6
+    assert cov < 6e-4
+    assert np.linalg.norm(m) < 1e-3
+    assert drift < 1e-6

@@ -15,8 +15,9 @@ source width scaled with the box).
 * FP32 arithmetic with FP32 / FP16-deviation storage are run for the same number of steps
   from the same start and compared with the FP64 steady field.  Their per-step increments
   near steady state are below FP32 resolution, so each settles on its own rounding-level
-  fixed point: the error against FP64 is stated (FP32 4.2e-4, FP16 deviations 1.8e-4 rel L2
-  measured) and gated at about twice that.
+  fixed point: the error against FP64 is stated (FP32 with its default exact stored mass
+  9.6e-4, without it 4.2e-4; FP16 deviations 1.8e-4 rel L2 measured) and gated at about twice
+  that.
 """
 import numpy as np
 import pytest
@@ -101,7 +102,7 @@ def test_steady_state_is_the_oracles_fixed_point(twin, steady64):
     assert rel_l2(g1, g) < 1e-6          # populations: the fast flux modes have settled too
 
 
-@pytest.mark.parametrize("prec,bound", [("f32", 1e-3), ("f16dev", 5e-4)])
+@pytest.mark.parametrize("prec,bound", [("f32", 2e-3), ("f16dev", 5e-4)])
 def test_reduced_forms_reach_the_same_steady_field(E, twin, steady64, prec, bound):
     lat = _lattice(E, twin, prec)
     E.elbm_step(lat.h, steady64["steps"] - 1)
