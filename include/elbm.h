@@ -148,7 +148,8 @@ elbm_status elbm_set_step_kernel(elbm_handle h, int32_t variant);
  * summation (the deviation storages keep their mass exactly by construction, FP64 to its
  * rounding).  With on = 0 the rounding of the updates acts as a small correlated source: on
  * the 256^3 plume of Section 3.1 the total mass drifts by 7.5e-4 over 40 000 steps (1e-7 with
- * on = 1).  Costs about 1 % of the FP32 step time.  ELBM_ERR_ARG unless on is 0 or 1. */
+ * on = 1).  Costs 1 to 4 % of the FP32 step time (more where the collision, not HBM, sets the
+ * pace).  ELBM_ERR_ARG unless on is 0 or 1. */
 elbm_status elbm_set_exact_mass(elbm_handle h, int32_t on);
 
 /* The implementation (1 or 2, as above) elbm_step launches with the handle's current
