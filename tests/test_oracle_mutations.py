@@ -83,3 +83,63 @@ def test_flipped_correction_sign_is_caught(monkeypatch):
         return lam - 2 * corr / hh
     monkeypatch.setattr(E, "entropic_amplitude", bad)
     assert _root_gap() > 5e-2
+
+
+# ---- pins of the tensor parametrisation, the entropy diagnostic and the misfit gradient
+
+def _table1_gap():
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+    blk = gold["table1_gaussian_tensor_targets"]
+    worst = 0.0
+    for row in blk["rows"]:
+        th = torch.tensor([math.log(v) for v in row["d"]] + [math.radians(a) for a in blk["euler_deg"]],
+                          dtype=torch.float64)
+        D = O.tensor_from_params(th)
+        d6 = torch.stack([D[0, 0], D[0, 1], D[0, 2], D[1, 1], D[1, 2], D[2, 2]]).numpy() * 1e3
+        worst = max(worst, float(np.abs(d6 - np.asarray(row["target_1e3"])).max()))
+    return worst
+
+
+def _entropy_gap():
+    phi = np.random.default_rng(3).uniform(0.05, 2.0, (3, 4, 5))
+    g = O.equilibrium(torch.as_tensor(phi), torch.zeros(3, dtype=torch.float64))
+    return abs(O.diagnostics(g)["entropy"] - float(np.sum(phi * np.log(phi)))) / abs(float(np.sum(phi * np.log(phi))))
+
+
+def test_unmutated_baseline_params_entropy():
+    assert _table1_gap() < 5.5e-5
+    assert _entropy_gap() < 1e-13
+
+
+def test_transposed_rotation_is_caught(monkeypatch):
+    orig = E.rotation_zyz
+    monkeypatch.setattr(E, "rotation_zyz", lambda a, b, c: orig(a, b, c).transpose(-1, -2))
+    assert _table1_gap() > 1e-3
+
+
+def test_swapped_euler_order_is_caught(monkeypatch):
+    orig = E.rotation_zyz
+    monkeypatch.setattr(E, "rotation_zyz", lambda a, b, c: orig(c, b, a))
+    assert _table1_gap() > 1e-3
+
+
+def test_entropy_without_weights_is_caught(monkeypatch):
+    # H computed as sum g ln g (the W_i dropped from Eq. method-entropy)
+    monkeypatch.setattr(E, "W", torch.ones(27, dtype=torch.float64))
+    assert _entropy_gap() > 1e-3
+
+
+def test_gradient_lost_through_checkpoints_is_caught(monkeypatch):
+    """Re-entrant checkpointing computes gradients only for a segment's tensor inputs, so the
+    dependence on theta through the relaxation matrix captured by the segment is dropped."""
+    import oracle.adjoint as A
+    from test_oracle_adjoint import _fd_errors
+    from torch.utils.checkpoint import checkpoint as ck
+    monkeypatch.setattr(A, "checkpoint", lambda f, *a, **k: ck(f, *a, use_reentrant=True))
+    try:
+        err, _ = _fd_errors(segment=2)
+    except RuntimeError:          # nothing left that requires a gradient
+        err = float("inf")
+    assert err > 1e-3
