@@ -38,3 +38,33 @@ def mode_history(k, S, phi_hat0, nsteps):
         v = A @ v
         out.append(v[0])
     return np.array(out)
+
+
+# ---- the same recurrence on the two-dimensional set D2Q9 (3 x 3 amplification matrix)
+_C2 = np.array(list(itertools.product((-1, 0, 1), repeat=2)), dtype=float)
+_M2 = (_C2 != 0).sum(1)
+_W2 = (2.0 / 3.0) ** (2 - _M2) * (1.0 / 6.0) ** _M2
+
+
+def amplification_2d(k, S):
+    A = np.zeros((3, 3), dtype=complex)
+    ImS = np.eye(2) - S
+    for i in range(9):
+        ph = np.exp(-1j * (_C2[i] @ k))
+        A += _W2[i] * ph * np.outer(np.r_[1.0, _C2[i]], np.r_[1.0, 3.0 * (_C2[i] @ ImS)])
+    return A
+
+
+def dominant_rate_2d(k, S):
+    ev = np.linalg.eigvals(amplification_2d(k, S))
+    return -np.log(np.abs(ev[np.argmax(np.abs(ev))]))
+
+
+def mode_history_2d(k, S, phi_hat0, nsteps):
+    A = amplification_2d(k, S)
+    v = np.array([phi_hat0, 0, 0], dtype=complex)
+    out = []
+    for _ in range(nsteps):
+        v = A @ v
+        out.append(v[0])
+    return np.array(out)

@@ -143,3 +143,50 @@ def test_gradient_lost_through_checkpoints_is_caught(monkeypatch):
     except RuntimeError:          # nothing left that requires a gradient
         err = float("inf")
     assert err > 1e-3
+
+
+# ---- D2Q9 oracle
+
+def _fourier_gap_2d():
+    import oracle.d2q9 as O2
+    from fourier_pin import mode_history_2d
+    nx, ny, m = 9, 7, (2, -1)
+    y, x = np.meshgrid(np.arange(ny, dtype=float), np.arange(nx, dtype=float), indexing="ij")
+    k = 2 * math.pi * np.array([m[0] / nx, m[1] / ny])
+    phi0 = 1.0 + 0.1 * np.sin(k[0] * x + k[1] * y)
+    a = 0.7
+    R = np.array([[math.cos(a), -math.sin(a)], [math.sin(a), math.cos(a)]])
+    D = R @ np.diag([0.05, 0.005]) @ R.T
+    prob = O2.Problem.from_tensor((0.0, 0.0), D)
+    idx = (m[1] % ny, m[0] % nx)
+    hist = []
+    O2.run(O2.init_equilibrium(phi0, (0.0, 0.0)), prob, 20,
+           callback=lambda n, g: hist.append(np.fft.fft2(g.sum(0).numpy())[idx]))
+    S = np.linalg.inv(0.5 * np.eye(2) + 3.0 * D)
+    pred = mode_history_2d(k, S, np.fft.fft2(phi0)[idx], 20)
+    return np.max(np.abs(np.array(hist) - pred)) / abs(np.fft.fft2(phi0)[idx])
+
+
+def test_unmutated_baseline_2d():
+    assert _fourier_gap_2d() < 1e-12
+
+
+def test_2d_wrong_lift_normalisation_is_caught(monkeypatch):
+    import oracle.d2q9 as O2
+    orig = O2.lift
+    monkeypatch.setattr(O2, "lift", lambda a: 0.5 * orig(a))
+    assert _fourier_gap_2d() > 1e-3
+
+
+def test_2d_transposed_streaming_axes_is_caught(monkeypatch):
+    """Streaming that rolls x along the y axis and y along the x axis (an oblique mode on a
+    non-square grid sees it)."""
+    import oracle.d2q9 as O2
+
+    def bad(gp):
+        out = torch.empty_like(gp)
+        for i, (cx, cy) in enumerate(O2.C_INT):
+            out[i] = torch.roll(gp[i], shifts=(cx, cy), dims=(0, 1))
+        return out
+    monkeypatch.setattr(O2, "stream", bad)
+    assert _fourier_gap_2d() > 1e-3
