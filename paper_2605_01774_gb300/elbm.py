@@ -66,6 +66,7 @@ def lib() -> C.CDLL:
         "elbm_set_source_amplitude": (S, [H, C.c_double]),
         "elbm_set_lambda_mode": (S, [H, C.c_int32]),
         "elbm_set_step_kernel": (S, [H, C.c_int32]),
+        "elbm_set_wait_limit": (S, [H, I64]),
         "elbm_get_step_kernel": (S, [H, C.POINTER(C.c_int32)]),
         "elbm_set_exact_mass": (S, [H, C.c_int32]),
         "elbm_storage_projections": (S, [H, C.POINTER(C.c_int64)]),
@@ -111,6 +112,25 @@ def lib() -> C.CDLL:
         "elbm_adjoint_configure": (S, [H, D, C.c_double, I32]),
         "elbm_adjoint_misfit": (S, [H, P, P, I64, I32, PI64, P, D, P, PI64]),
         "elbm_adjoint_step": (S, [H, P, P, P, P, P, P]),
+    })
+    sig.update({
+        "elbm2d_create": (S, [C.POINTER(C.c_int64), S, P, C.POINTER(H)]),
+        "elbm2d_destroy": (None, [H]),
+        "elbm2d_last_error": (C.c_char_p, [H]),
+        "elbm2d_set_params": (S, [H, C.POINTER(elbm_params)]),
+        "elbm2d_set_tensor_uniform": (S, [H, D]),
+        "elbm2d_set_tensor_field": (S, [H, P]),
+        "elbm2d_set_velocity_uniform": (S, [H, D]),
+        "elbm2d_set_velocity_field": (S, [H, P]),
+        "elbm2d_init_equilibrium": (S, [H, P, S]),
+        "elbm2d_write_populations": (S, [H, P, S]),
+        "elbm2d_read_populations": (S, [H, P, S]),
+        "elbm2d_read_moments": (S, [H, P, S]),
+        "elbm2d_step": (S, [H, I64]),
+        "elbm2d_reduce": (S, [H, D, D, D, C.POINTER(C.c_int64)]),
+        "elbm2d_synchronize": (S, [H]),
+        "elbm2d_check_velocity": (S, [D]),
+        "elbm2d_relaxation_complement": (S, [D, D]),
     })
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -215,6 +235,10 @@ def elbm_set_lambda_mode(h, mode):
 
 def elbm_set_step_kernel(h, variant):
     _check(lib().elbm_set_step_kernel(h, int(variant)), h)
+
+
+def elbm_set_wait_limit(h, cycles):
+    _check(lib().elbm_set_wait_limit(h, int(cycles)), h)
 
 
 def elbm_set_exact_mass(h, on):
@@ -494,3 +518,109 @@ def elbm_fma_peak(prec="f64") -> float:
     v = C.c_double(0.0)
     _check(lib().elbm_fma_peak(PRECISIONS[prec], C.byref(v)))
     return float(v.value)
+
+
+# ------------------------------------------------------------------- D2Q9 (include/elbm2d.h)
+def _check2(status: int, h=None):
+    if status != 0:
+        msg = lib().elbm2d_last_error(h).decode() if h else ""
+        raise ElbmError(status, msg)
+
+
+def elbm2d_create(dims, prec="f32", stream=None):
+    d = (C.c_int64 * 2)(*[int(v) for v in dims])
+    h = C.c_void_p()
+    _check2(lib().elbm2d_create(d, PRECISIONS[prec] if isinstance(prec, str) else int(prec), _stream_ptr(stream),
+                                C.byref(h)))
+    return h
+
+
+def elbm2d_destroy(h):
+    lib().elbm2d_destroy(h)
+
+
+def elbm2d_set_params(h, theta, eps=0.0, fallback=True):
+    p = elbm_params(float(theta), float(eps), 1 if fallback else 0)
+    _check2(lib().elbm2d_set_params(h, C.byref(p)), h)
+
+
+def elbm2d_set_tensor_uniform(h, D3):
+    _check2(lib().elbm2d_set_tensor_uniform(h, _d(D3, 3)), h)
+
+
+def elbm2d_set_tensor_field(h, D3):
+    _check2(lib().elbm2d_set_tensor_field(h, _ptr(D3)), h)
+
+
+def elbm2d_set_velocity_uniform(h, u):
+    _check2(lib().elbm2d_set_velocity_uniform(h, _d(u, 2)), h)
+
+
+def elbm2d_set_velocity_field(h, u2):
+    _check2(lib().elbm2d_set_velocity_field(h, _ptr(u2)), h)
+
+
+def elbm2d_init_equilibrium(h, phi0):
+    _check2(lib().elbm2d_init_equilibrium(h, _ptr(phi0), _dtype_code(phi0)), h)
+
+
+def elbm2d_write_populations(h, g):
+    _check2(lib().elbm2d_write_populations(h, _ptr(g), _dtype_code(g)), h)
+
+
+def elbm2d_read_populations(h, out):
+    _check2(lib().elbm2d_read_populations(h, _ptr(out), _dtype_code(out)), h)
+    return out
+
+
+def elbm2d_read_moments(h, phi_out):
+    _check2(lib().elbm2d_read_moments(h, _ptr(phi_out), _dtype_code(phi_out)), h)
+    return phi_out
+
+
+def elbm2d_step(h, nsteps=1):
+    _check2(lib().elbm2d_step(h, int(nsteps)), h)
+
+
+def elbm2d_reduce(h, allow_nonfinite=False):
+    m, e, g = C.c_double(), C.c_double(), C.c_double()
+    fb = C.c_int64()
+    st = lib().elbm2d_reduce(h, C.byref(m), C.byref(e), C.byref(g), C.byref(fb))
+    if st != 0 and not (allow_nonfinite and st == 6):
+        _check2(st, h)
+    return dict(mass=m.value, entropy=e.value, gmin=g.value, n_fallback=fb.value, status=st)
+
+
+def elbm2d_synchronize(h):
+    _check2(lib().elbm2d_synchronize(h), h)
+
+
+def elbm2d_check_velocity(u) -> int:
+    return int(lib().elbm2d_check_velocity(_d(u, 2)))
+
+
+def elbm2d_relaxation_complement(D3):
+    out = (C.c_double * 3)()
+    _check2(lib().elbm2d_relaxation_complement(_d(D3, 3), out))
+    return np.array(out[:])
+
+
+class Lattice2D:
+    """Owning wrapper over one D2Q9 handle (marshalling only)."""
+
+    def __init__(self, dims, prec="f32", stream=None):
+        self.dims = tuple(int(v) for v in dims)
+        self.N = self.dims[0] * self.dims[1]
+        self.prec = prec
+        self.h = elbm2d_create(self.dims, prec, stream)
+
+    def close(self):
+        if self.h is not None:
+            elbm2d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -179,9 +179,13 @@ SOLID_EIG = (1e-2, 1e-4, 1e-6)
 
 
 def heterogeneous(n=384, seed=3, steps=50, porosity=0.6, src_amp=1e-4, src_width=16.0,
-                  dims=None) -> Workload:
+                  dims=None, shift=1.0) -> Workload:
     """Two-phase porous medium with a smooth rotation field, Gaussian source and
-    Dirichlet x-faces (phi = 1 at x = -1/2, phi = 0 at x = Nx - 1/2); u = 0.
+    Dirichlet x-faces (phi = 1 + shift at x = -1/2, phi = shift at x = Nx - 1/2); u = 0.
+
+    The scalar is shifted by a constant, as Section 3.3 does for fields that would reach
+    zero, so that the populations stay positive: with shift = 0 the outlet face keeps the
+    positivity fallback firing and the run does not reach steady state.
 
     Pore principal values (3e-2, 3e-3, 1e-6), solid (1e-2, 1e-4, 1e-6): the
     largest local contrast is 3e-2 / 1e-6 = 3e4.  The ZYZ angles vary as
@@ -217,10 +221,10 @@ def heterogeneous(n=384, seed=3, steps=50, porosity=0.6, src_amp=1e-4, src_width
     mu = tuple((d - 1) / 2.0 for d in dims)
     src = gaussian(dims, mu, src_width, peak=src_amp)
     # linear initial profile between the two Dirichlet values
-    phi0 = 1.0 - (x + 0.5) / dims[0]
+    phi0 = shift + 1.0 - (x + 0.5) / dims[0]
     return Workload(name=f"heterogeneous_{dims[0]}x{dims[1]}x{dims[2]}", dims=dims, steps=steps,
-                    u=np.zeros(3), D6_field=D6, phi0=phi0, source=src, dirichlet_x=(1.0, 0.0),
-                    meta=dict(mask=mask, seed=seed, porosity=float(mask.mean())))
+                    u=np.zeros(3), D6_field=D6, phi0=phi0, source=src, dirichlet_x=(1.0 + shift, shift),
+                    meta=dict(mask=mask, seed=seed, porosity=float(mask.mean()), shift=shift))
 
 
 def batched_domains(ndom=512, seed=4, nmin=16, nmax=96, steps=500):
@@ -266,3 +270,24 @@ def adjoint_problem(n=64, seed=5, steps=500, obs=(250, 500), u=(0.02, 0.0, 0.0),
     phi0 = 0.1 + gaussian(dims, mu, sigma)
     return dict(theta_true=th, theta0=th0, phi0=phi0, u=np.asarray(u, np.float64),
                 obs=tuple(obs), steps=steps, dims=dims)
+
+
+def channel2d(nx=4096, ny=4096, seed=11, U=0.04, drift=0.01, d1=0.03, steps=200):
+    """Two-dimensional fields shaped like Section 4.1's channel problem on a periodic box:
+    a streamwise velocity U (1 + sin(2 pi (y + 1/2)/Ny))/2 with a weaker wall-normal drift
+    -drift cos(2 pi y / Ny), and a tensor whose principal values and orientation vary across
+    the channel (d1 (1 + 0.3 s), d2 (1 + 0.2 cos), angle 0.6 + 0.8 s + 0.1 sin(2 pi x / Nx),
+    s = sin(2 pi (y + 1/2)/Ny), d2 log-uniform in [1e-4, 1e-2] from `seed`); initial field
+    1 + a Gaussian bump.  Returns (u [2, Ny, Nx], D3 [3, Ny, Nx] as (Dxx, Dxy, Dyy), phi0)."""
+    g = rng(seed)
+    y = np.arange(ny, dtype=np.float64)[:, None] * np.ones((1, nx))
+    x = np.ones((ny, 1)) * np.arange(nx, dtype=np.float64)[None, :]
+    s = np.sin(2 * math.pi * (y + 0.5) / ny)
+    u = np.stack([U * (0.5 + 0.5 * s), -drift * np.cos(2 * math.pi * y / ny)])
+    ang = 0.6 + 0.8 * s + 0.1 * np.sin(2 * math.pi * x / nx)
+    a = d1 * (1 + 0.3 * s)
+    b = 10 ** g.uniform(-4, -2) * (1 + 0.2 * np.cos(2 * math.pi * y / ny))
+    c, sn = np.cos(ang), np.sin(ang)
+    D3 = np.stack([c * c * a + sn * sn * b, c * sn * (a - b), sn * sn * a + c * c * b])
+    phi0 = 1.0 + 0.5 * np.exp(-((x - nx / 2) ** 2 / (2 * (nx / 6) ** 2) + (y - ny / 2) ** 2 / (2 * (ny / 5) ** 2)))
+    return u, D3, phi0

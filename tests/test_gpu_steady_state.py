@@ -46,10 +46,7 @@ def E():
 
 @pytest.fixture(scope="module")
 def twin():
-    wl = synth.heterogeneous(dims=(N, N, N), src_width=16.0 * N / 384)
-    wl.phi0 = wl.phi0 + SHIFT
-    wl.dirichlet_x = (wl.dirichlet_x[0] + SHIFT, wl.dirichlet_x[1] + SHIFT)
-    return wl
+    return synth.heterogeneous(dims=(N, N, N), src_width=16.0 * N / 384, shift=SHIFT)
 
 
 def _lattice(E, wl, prec):
