@@ -26,7 +26,11 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) double g_scratch[4 * kMaxPartials + 4];
 
 std::mutex g_mu;
-double* g_scratch_dev[kMaxDevices] = {};  // device address of g_scratch, per device
+// Device address of g_scratch per device, and the id of the context it was looked up in: a
+// module's __device__ arrays are placed anew when a device's context is destroyed and
+// re-created (cudaDeviceReset), so the address is looked up again when the id changes.
+double* g_scratch_dev[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
 
 template <typename Elem>
 __global__ void __launch_bounds__(256)
@@ -117,18 +121,49 @@ __global__ void __launch_bounds__(256) k_final_strided(const double* __restrict_
   }
 }
 
-// Device address of g_scratch on the current device, looked up once per device.
+// Unique id of the current context (driver entry points fetched through the runtime, so the
+// library needs no link against the driver library); 0 if it cannot be had.
+unsigned long long current_context_id() {
+  typedef int (*get_current_t)(void**);
+  typedef int (*get_id_t)(void*, unsigned long long*);
+  static get_current_t get_current = nullptr;
+  static get_id_t get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<get_current_t>(f1);
+      get_id = reinterpret_cast<get_id_t>(f2);
+    }
+    cudaGetLastError();
+    looked_up = true;
+  }
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current && get_id && get_current(&ctx) == 0 && ctx != nullptr && get_id(ctx, &id) == 0) return id;
+  return 0;
+}
+
+// Device address of g_scratch on the current device: looked up (cudaGetSymbolAddress, with
+// the device current) on the first call in each context of that device, then cached.
 cudaError_t scratch_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (g_scratch_dev[dev] == nullptr) {
+  const unsigned long long ctx = current_context_id();
+  if (g_scratch_dev[dev] == nullptr || ctx == 0 || ctx != g_scratch_ctx[dev]) {
     double* p = nullptr;
     e = cudaGetSymbolAddress((void**)&p, g_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_dev[dev] = p;
+    // the symbol lookup made the runtime create the context if there was none yet
+    g_scratch_ctx[dev] = ctx != 0 ? ctx : current_context_id();
   }
   *out = g_scratch_dev[dev];
   return cudaSuccess;
@@ -178,6 +213,9 @@ extern "C" elbm_status elbm_reduce_noalloc(const void* pops, const float* scale,
   if (!pops || !dims || !u || !out4) return ELBM_ERR_ARG;
   if ((int)prec < 0 || (int)prec > 3) return ELBM_ERR_ARG;
   if (prec >= ELBM_F32_F16DEV && !scale) return ELBM_ERR_ARG;
+  // the kernels read these directly: a host pointer here would make them fault
+  if (!device_ptr(pops) || (prec >= ELBM_F32_F16DEV && !device_ptr(scale)) || (source && !device_ptr(source)))
+    return ELBM_ERR_ARG;
   for (int a = 0; a < 3; ++a)
     if (dims[a] < 1 || dims[a] > 65535) return ELBM_ERR_ARG;
   const double N = (double)dims[0] * (double)dims[1] * (double)dims[2];
