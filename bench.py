@@ -38,7 +38,7 @@ import synth  # noqa: E402
 
 METRIC = "ELBM-ADE MLUPS & % HBM roofline, chosen vs plain form at stated L2 error"
 UNIT = "MLUPS"
-KERNEL_NAME = {1: "k_step", 2: "k_step_rows"}
+KERNEL_NAME = {1: "k_step", 2: "k_step_rows", 3: "k_step_pipe"}
 F64_FLOPS_PER_NODE = 706   # mean of the two launches in profiles/k_step_fp64_plume128_flops.md
 BYTES_PER_NODE = {"f64": 27 * 8 * 2, "f32": 27 * 4 * 2, "f16dev": (27 * 2 + 4) * 2, "bf16dev": (27 * 2 + 4) * 2}
 WORKLOAD = ("advected anisotropic Gaussian plume 256^3 periodic, u=(0.05,0.03,0.02), "
@@ -241,6 +241,7 @@ def run_ours(args, rank, world, local, dist):
     headline = args.form
     order = [headline] + [f for f in ("f32", "bf16dev", "f16dev") if f != headline]
     clocks = None
+    late = None
     for prec in order:
         lat = make(prec)
         ms, ck = timed(lat, args.steps, args.warmup, sample_clocks=(prec == headline))
@@ -249,6 +250,8 @@ def run_ours(args, rank, world, local, dist):
         d = E.elbm_reduce(lat.h, allow_nonfinite=True)
         proj = E.elbm_storage_projections(lat.h)
         kern = KERNEL_NAME[E.elbm_get_step_kernel(lat.h)]
+        if prec == headline and args.late_window > 0:
+            late = late_window(args, E, lat, stream, dev, dist, N, d["n_fallback"], local)
         lat.close()
         ms_max = max_over_ranks(ms, dist, dev)
         forms[prec] = dict(ms_per_step=ms_max / args.steps,
@@ -317,6 +320,11 @@ def run_ours(args, rank, world, local, dist):
                final_mass=mass)
 
     batched = None if args.batched_steps <= 0 else run_batched(args, E, dev, dist, world)
+    extra = {}
+    if not args.skip_extra:
+        extra["heterogeneous"] = run_heterogeneous(args, E, dev, stream, dist, world)
+        extra["adjoint"] = run_adjoint(args, E, dev, dist, world)
+        extra["d2q9"] = run_d2q9(args, E, dev, stream, dist, world)
 
     if rank != 0:
         return None
@@ -346,13 +354,209 @@ def run_ours(args, rank, world, local, dist):
         "chosen_vs_plain_speedup": hf["mlups"] / forms["f32"]["mlups"],
         "vs_plain_speedup": {p: forms[p]["mlups"] / forms["f32"]["mlups"] for p in order + ["f64"]},
         "e2e": e2e,
+        "late_window": late,
         "batched": batched,
+        **extra,
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     return line
+
+
+def late_window(args, E, lat, stream, dev, dist, N, fb_so_far, local):
+    """The headline form's rate late in the run: the same lattice advanced (untimed) to step
+    `late_start`, then `late_window` steps timed with CUDA events on the launching stream, with
+    the fallback fraction of those steps and the SM clocks sampled meanwhile."""
+    import torch
+    done = E.elbm_get_step(lat.h)
+    if args.late_start > done:
+        E.elbm_step(lat.h, args.late_start - done)
+    fb0 = E.elbm_reduce(lat.h, allow_nonfinite=True)["n_fallback"]
+    stream.synchronize()
+    barrier(dist)
+    sampler = ClockSampler(local)
+    sampler.__enter__()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    E.elbm_step(lat.h, args.late_window)
+    ev1.record(stream)
+    ev1.synchronize()
+    sampler.__exit__(None, None, None)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev) / args.late_window
+    fb1 = E.elbm_reduce(lat.h, allow_nonfinite=True)["n_fallback"]
+    peak, _ = measured_peaks()
+    bpn = BYTES_PER_NODE[args.form]
+    return {"steps": [args.late_start, args.late_start + args.late_window], "ms_per_step": ms,
+            "mlups": N / (ms * 1e-3) / 1e6, "hbm_frac_of_measured": bpn * N / (ms * 1e-3) / 1e9 / peak,
+            "fallback_node_fraction": (fb1 - fb0) / (args.late_window * N),
+            "fallback_node_fraction_timed_window": fb_so_far / ((args.steps + args.warmup) * N),
+            "clocks": sampler.summary()}
+
+
+def _time_steps(E, step_fn, K, stream):
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    step_fn(K)
+    ev1.record(stream)
+    ev1.synchronize()
+    return ev0.elapsed_time(ev1) / K
+
+
+def run_heterogeneous(args, E, dev, stream, dist, world):
+    """Two-phase porous transport at 384^3 (per-node tensor field from a seeded rotation field
+    and porous mask, Gaussian source, Dirichlet x faces at the shifted values 2 and 1, u = 0):
+    ms/step, MLUPS and HBM fraction per form (bytes: populations read and written, the per-node
+    T field and the FP32 source plane), and the relative L2 error of phi against the FP64 form
+    after `het_err_steps` steps from the same start.  The run to steady state of this workload
+    is checked on a 48^3 twin in the tests (about 2e5 steps there; 1.5e6 at 384^3)."""
+    import torch
+    hw = synth.heterogeneous(n=args.het_size)
+    Nh = int(np.prod(hw.dims))
+    D6 = torch.as_tensor(hw.D6_field, dtype=torch.float32, device=dev)
+    src = torch.as_tensor(hw.source, dtype=torch.float32, device=dev)
+    phi0 = torch.as_tensor(hw.phi0, dtype=torch.float32, device=dev)
+    del hw.D6_field
+    peak, _ = measured_peaks()
+
+    def make(prec):
+        lat = E.Lattice(hw.dims, prec, bc=hw.dirichlet_x, stream=stream)
+        E.elbm_set_tensor_field(lat.h, D6)
+        E.elbm_set_source(lat.h, src)
+        E.elbm_set_params(lat.h, theta=THETA)
+        stream.wait_stream(torch.cuda.current_stream(dev))
+        E.elbm_init_equilibrium(lat.h, phi0)
+        return lat
+
+    out = {"workload": "two-phase porous 384^3, per-node tensor field, Gaussian source, Dirichlet x (2, 1), u = 0",
+           "nodes": Nh * world, "err_steps": args.het_err_steps, "forms": {}}
+    phis = {}
+    for prec in ("f64", "f32", "f16dev", "bf16dev"):
+        lat = make(prec)
+        E.elbm_step(lat.h, args.het_err_steps)
+        ph = torch.empty(hw.dims[::-1], dtype=torch.float64, device=dev)
+        with torch.cuda.stream(stream):
+            E.elbm_read_moments(lat.h, ph)
+        E.elbm_step(lat.h, 3)
+        stream.synchronize()
+        barrier(dist)
+        K = args.het_steps if prec != "f64" else max(5, args.het_steps // 10)
+        ms = max_over_ranks(_time_steps(E, lambda k: E.elbm_step(lat.h, k), K, stream), dist, dev)
+        fb = E.elbm_reduce(lat.h, allow_nonfinite=True)["n_fallback"]
+        bpn = BYTES_PER_NODE[prec] + (48 if prec == "f64" else 24) + 4
+        mlups = world * Nh / (ms * 1e-3) / 1e6
+        out["forms"][prec] = {"kernel": KERNEL_NAME[E.elbm_get_step_kernel(lat.h)], "ms_per_step": ms, "mlups": mlups,
+                              "bytes_per_node": bpn, "hbm_frac_of_measured": bpn * mlups / world * 1e6 / 1e9 / peak,
+                              "n_fallback": fb}
+        lat.close()
+        phis[prec] = ph
+    ref = phis["f64"]
+    for prec in ("f32", "f16dev", "bf16dev"):
+        out["forms"][prec]["rel_l2_phi_vs_fp64"] = float(torch.linalg.vector_norm(phis[prec] - ref) /
+                                                         torch.linalg.vector_norm(ref))
+    f32 = out["forms"]["f32"]["mlups"]
+    out["vs_plain_speedup"] = {p: out["forms"][p]["mlups"] / f32 for p in out["forms"]}
+    return out
+
+
+def run_adjoint(args, E, dev, dist, world):
+    """Inverse problem on a 64^3 box, FP32: per-node (ln d, ZYZ angles) field, u = (0.02, 0, 0),
+    500 steps, misfit against snapshots at 250 and 500 from the true field, checkpoints every
+    50 steps.  Times the forward sweep alone (the misfit) and the full gradient (forward sweep,
+    then per 50-step segment a recomputation and the reverse sweep of hand-written
+    vector-Jacobian products); the reverse rate is derived as (gradient - 2 forward) / steps.
+    Bytes per node-update: forward 240 (populations in and out, the FP32 T field), one VJP step
+    444 (forward populations, adjoint populations in and out, T, the FP64 T accumulator read and
+    written).  At 64^3 the working set (63 MB per forward step) fits in L2, so these are rates,
+    not HBM-roofline fractions."""
+    import torch
+    p = synth.adjoint_problem(n=args.adj_size, steps=args.adj_steps, obs=(args.adj_steps // 2, args.adj_steps))
+    dims, N = p["dims"], int(np.prod(p["dims"]))
+    th_true = torch.as_tensor(p["theta_true"], dtype=torch.float32, device=dev)
+    th0 = torch.as_tensor(p["theta0"], dtype=torch.float32, device=dev)
+    phi0 = torch.as_tensor(p["phi0"], dtype=torch.float32, device=dev)
+    # targets: phi of the true field at the observation steps, from the single-lattice path
+    lat = E.Lattice(dims, "f32")
+    E.elbm_set_tensor_params_field(lat.h, th_true)
+    E.elbm_set_velocity_uniform(lat.h, p["u"])
+    E.elbm_set_params(lat.h, theta=1e-8)
+    E.elbm_init_equilibrium(lat.h, phi0)
+    tg = torch.empty((2,) + dims[::-1], dtype=torch.float32, device=dev)
+    t = 0
+    for o, ts in enumerate(p["obs"]):
+        E.elbm_step(lat.h, ts - t)
+        t = ts
+        E.elbm_read_moments(lat.h, tg[o])
+    torch.cuda.synchronize()
+    lat.close()
+    h = E.elbm_adjoint_create(dims, "f32")
+    E.elbm_adjoint_configure(h, p["u"], 1e-8, 50)
+    grad = torch.empty((6,) + dims[::-1], dtype=torch.float32, device=dev)
+    E.elbm_adjoint_misfit(h, th0, phi0, p["steps"], p["obs"], tg, grad)       # warm-up
+    barrier(dist)
+    t0 = time.perf_counter()
+    J, _ = E.elbm_adjoint_misfit(h, th0, phi0, p["steps"], p["obs"], tg)[:2]
+    t_fwd = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    t0 = time.perf_counter()
+    res = E.elbm_adjoint_misfit(h, th0, phi0, p["steps"], p["obs"], tg, grad)
+    t_grad = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    E.elbm_adjoint_destroy(h)
+    S = p["steps"]
+    fwd = t_fwd * 1e3 / S
+    rev = max(t_grad - 2 * t_fwd, 1e-9) * 1e3 / S
+    return {"workload": "64^3 inverse problem, FP32, 500 steps, obs 250/500, checkpoints every 50",
+            "nodes": N * world, "steps": S, "J": float(J), "n_fallback": int(res[-1]),
+            "forward_ms_per_step": fwd, "forward_mlups": world * N / (fwd * 1e-3) / 1e6,
+            "forward_bytes_per_node": 240, "forward_gbs": 240 * N / (fwd * 1e-3) / 1e9,
+            "gradient_ms_per_step": t_grad * 1e3 / S, "reverse_ms_per_step": rev,
+            "reverse_mlups": world * N / (rev * 1e-3) / 1e6, "reverse_bytes_per_node": 444,
+            "reverse_gbs": 444 * N / (rev * 1e-3) / 1e9,
+            "note": "host wall clock per call (synchronous API); 63 MB working set is L2-resident"}
+
+
+def run_d2q9(args, E, dev, stream, dist, world):
+    """D2Q9 (Section 2.1's second velocity set) on a 4096^2 periodic box with channel-shaped
+    per-node velocity and tensor fields (Section 4.1's shape): ms/step, MLUPS, bytes per node
+    (9 populations read and written, the per-node T field and the FP32 velocity field), HBM
+    fraction, and phi after `d2_err_steps` steps against the FP64 form."""
+    import torch
+    n = args.d2_size
+    uf, D3, phi0 = synth.channel2d(n, n, 11)
+    uf = torch.as_tensor(uf, dtype=torch.float32, device=dev)
+    D3 = torch.as_tensor(D3, dtype=torch.float32, device=dev)
+    phi0 = torch.as_tensor(phi0, dtype=torch.float32, device=dev)
+    peak, _ = measured_peaks()
+    out = {"workload": f"D2Q9 {n}x{n} periodic, per-node velocity and tensor fields", "nodes": n * n * world,
+           "forms": {}}
+    phis = {}
+    for prec in ("f64", "f32"):
+        lat = E.Lattice2D((n, n), prec, stream=stream)
+        E.elbm2d_set_tensor_field(lat.h, D3)
+        E.elbm2d_set_velocity_field(lat.h, uf)
+        E.elbm2d_set_params(lat.h, theta=THETA)
+        stream.wait_stream(torch.cuda.current_stream(dev))
+        E.elbm2d_init_equilibrium(lat.h, phi0)
+        E.elbm2d_step(lat.h, args.d2_err_steps)
+        ph = torch.empty((n, n), dtype=torch.float64, device=dev)
+        with torch.cuda.stream(stream):
+            E.elbm2d_read_moments(lat.h, ph)
+        stream.synchronize()
+        barrier(dist)
+        ms = max_over_ranks(_time_steps(E, lambda k: E.elbm2d_step(lat.h, k), args.d2_steps, stream), dist, dev)
+        es = 8 if prec == "f64" else 4
+        bpn = 2 * 9 * es + 3 * es + 8
+        mlups = world * n * n / (ms * 1e-3) / 1e6
+        out["forms"][prec] = {"ms_per_step": ms, "mlups": mlups, "bytes_per_node": bpn,
+                              "hbm_frac_of_measured": bpn * mlups / world * 1e6 / 1e9 / peak,
+                              "n_fallback": E.elbm2d_reduce(lat.h, allow_nonfinite=True)["n_fallback"]}
+        lat.close()
+        phis[prec] = ph
+    out["forms"]["f32"]["rel_l2_phi_vs_fp64"] = float(torch.linalg.vector_norm(phis["f32"] - phis["f64"]) /
+                                                      torch.linalg.vector_norm(phis["f64"]))
+    out["err_steps"] = args.d2_err_steps
+    return out
 
 
 def shard(items, rank, world):
@@ -406,9 +610,19 @@ def oracle_sample(n=40):
     return synth.gaussian_plume(n=n)
 
 
-def cpu_baseline(args, seconds=15.0):
-    import torch
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
+
+def _oracle_rate(args, seconds):
     import oracle as O
     wl = oracle_sample(args.cpu_sample)
     prob = O.Problem.from_tensor(wl.u, wl.D, theta=3e-4, lam_mode="literal")
@@ -419,9 +633,23 @@ def cpu_baseline(args, seconds=15.0):
         g = O.step(g, prob, n)
         n += 1
     dt = time.perf_counter() - t0
-    N = int(np.prod(wl.dims))
-    return {"value": N * n / dt / 1e6, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"{n} steps of the bench physics on a {wl.dims[0]}^3 periodic box (FP64, torch CPU)"}
+    return int(np.prod(wl.dims)) * n / dt / 1e6, n, wl.dims
+
+
+def cpu_baseline(args, seconds=15.0):
+    """The FP64 oracle on the host cores (all torch threads), then on one thread."""
+    import torch
+    threads = torch.get_num_threads()
+    v, n, dims = _oracle_rate(args, seconds)
+    torch.set_num_threads(1)
+    try:
+        v1, n1, _ = _oracle_rate(args, seconds / 2)
+    finally:
+        torch.set_num_threads(threads)
+    return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} steps of the bench physics on a {dims[0]}^3 periodic box (FP64, torch CPU)",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "single_thread": {"value": v1, "unit": UNIT, "threads": 1, "sample": f"{n1} steps, same box"}}
 
 
 def run_reference(args, rank, world, dist):
@@ -447,7 +675,7 @@ def run_reference(args, rank, world, dist):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": sample},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "cpu_model": cpu_model(), "nproc": os.cpu_count()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -465,12 +693,24 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=100,
                     help="steps per mode of the 512-domain sweep (0 skips it)")
-    ap.add_argument("--step-kernel", type=int, default=0, choices=[0, 1, 2],
-                    help="step implementation: 0 auto, 1 per-node gathers, 2 staged rows")
+    ap.add_argument("--step-kernel", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="step implementation: 0 auto, 1 per-node gathers, 2 staged rows, 3 pipelined rows")
     ap.add_argument("--workload", default="plume", choices=["plume", "heterogeneous"],
                     help="with --only: time the 256^3 plume (default) or the 384^3 heterogeneous workload")
     ap.add_argument("--only", default=None, choices=["f16dev", "bf16dev", "f32", "f64"],
                     help="time one form only (profiling runs)")
+    ap.add_argument("--late-start", type=int, default=1800, help="first step of the late window")
+    ap.add_argument("--late-window", type=int, default=200, help="steps timed late in the run (0 skips)")
+    ap.add_argument("--skip-extra", action="store_true",
+                    help="skip the heterogeneous, adjoint and D2Q9 workloads")
+    ap.add_argument("--het-size", type=int, default=384)
+    ap.add_argument("--het-steps", type=int, default=100)
+    ap.add_argument("--het-err-steps", type=int, default=20)
+    ap.add_argument("--adj-size", type=int, default=64)
+    ap.add_argument("--adj-steps", type=int, default=500)
+    ap.add_argument("--d2-size", type=int, default=4096)
+    ap.add_argument("--d2-steps", type=int, default=200)
+    ap.add_argument("--d2-err-steps", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -142,6 +142,18 @@ elbm_status elbm_set_lambda_mode(elbm_handle h, int32_t mode);
  * return ELBM_ERR_TIMEOUT. */
 elbm_status elbm_set_step_kernel(elbm_handle h, int32_t variant);
 
+/* Limit, in SM clock cycles, of every wait of the staged-row step kernels (variants 2 and 3)
+ * for a row's copies or a stage's release; cycles = 0 restores the default (2e9, about one
+ * second at 2 GHz).  A wait that runs out makes its block stop, wait (with the default limit)
+ * for the copies it issued, and leave; the next elbm_synchronize or elbm_reduce returns
+ * ELBM_ERR_TIMEOUT and the state is then undefined until the next elbm_init_* or
+ * elbm_write_populations.  Limits below 2^20 cycles are checked with non-blocking probes of
+ * the barrier (cycle-accurate); longer ones with blocking probes, which the hardware may
+ * hold for a short time of its own.  Meant for detecting a stalled device without hanging
+ * the host.
+ * ELBM_ERR_ARG if cycles < 0. */
+elbm_status elbm_set_wait_limit(elbm_handle h, int64_t cycles);
+
 /* FP32 storage only (no effect on the others): with on = 1 (the default) each node update
  * puts the rounding of its 27 post-collision values back on its rest population c = 0, so the
  * stored node mass equals the conserved phi of Eq. (method-collision) up to one FP32
@@ -284,18 +296,25 @@ elbm_status elbm_state_pointers(elbm_handle h, void** pops, void** scale);
  *
  * pops/scale: post-collision buffer in this library's storage layout for `prec`
  * (device pointers, e.g. from elbm_state_pointers; scale only for the deviation
- * formats, else NULL).  dims, u, bc: as given to the handle that produced the
- * state (bc NULL = periodic).  source: the FP32 source plane on the device, or
- * NULL.  out4: 4 doubles, host or device.  Work is ordered on cuda_stream; a
- * host out4 synchronises it.
+ * formats, else NULL).  dims, bc: as given to the handle that produced the state
+ * (bc NULL = periodic).  u: the handle's uniform velocity; (0, 0, 0) for a handle
+ * with a per-node velocity field (elbm_set_velocity_field), whose deviation
+ * storages encode against the zero-velocity equilibrium shape.  source: NULL, or
+ * the handle's FP32 source plane R on the device multiplied by the amplitude a of
+ * the source half-step the stored state includes (1 unless the amplitude was
+ * changed with elbm_set_source_amplitude or elbm_step_source_schedule, where it is
+ * the amplitude of the last step taken).  out4: 4 doubles, host or device.  Work is
+ * ordered on cuda_stream; a host out4 synchronises it.  pops, scale and source must
+ * be device memory of the current device (ELBM_ERR_ARG otherwise, nothing launched).
  *
  * Scratch: a fixed device array of 4096 partial sums (131 104 bytes per GPU
  * that loads the library, held until the process exits); the kernel strides over
  * the lattice, so every lattice the library accepts fits.  Lattices beyond the
  * library's limit (an axis above 65535, or 27 N >= 2^31) are rejected with
  * ELBM_ERR_ARG.  The first call on a device looks up the array's device address
- * (once per device, with that device current); make that first call before any
- * stream capture.  Every call reuses the same array and leaves its contents
+ * (once per device and context, with that device current; again after the context
+ * was destroyed and re-created, e.g. by cudaDeviceReset); make that first call before
+ * any stream capture.  Every call reuses the same array and leaves its contents
  * behind: calls that overlap on the GPU (other streams, other host threads on
  * the same device) race and must be serialised by the caller.
  * Errors: ELBM_ERR_ARG, ELBM_ERR_CUDA. */

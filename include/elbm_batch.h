@@ -60,7 +60,10 @@ elbm_status elbm_batch_init_equilibrium(elbm_batch_handle h, const float* phi0);
  *   mode 0: one persistent cooperative kernel for all steps (tiles taken round-robin,
  *           bounded grid barrier between steps), captured into a CUDA graph;
  *   mode 1: one batched launch per step over all tiles, the sequence captured into a graph;
- *   mode 2: one plain single-lattice launch per domain per step (reference path). */
+ *   mode 2: one plain single-lattice launch per domain per step (reference path).
+ * A graph is captured and instantiated on the first call with a given (mode, nsteps, state
+ * buffer parity, block shape, eps, fallback, wait limit) and relaunched by later calls with
+ * the same key (up to 8 kept per handle; the autotuner's shape changes discard them). */
 elbm_status elbm_batch_step(elbm_batch_handle h, int64_t nsteps, int32_t mode);
 
 /* Wait for the stream; ELBM_ERR_TIMEOUT if a barrier wait ran out. */

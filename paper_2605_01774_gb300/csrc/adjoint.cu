@@ -8,6 +8,10 @@
 // G^{n+1}_i(y + c_i).  One step's vector-Jacobian product is then a gather:
 //   Gbar^n(y) = J_C(G^n(y), T(y))^T [Gbar^{n+1}_i(y + c_i)]_i ,
 //   Tbar(y)  += d/dT of the same,
+// so every adjoint node update reads its 27 neighbours and writes only its own node: no
+// atomics.  (With a pull forward step the transpose would scatter into 27 neighbours.)  The
+// push stores are not scattered: for one population a warp writes 32 consecutive nodes shifted
+// by c_x, i.e. two 128-byte segments, the same access shape as the pull kernel's loads.
 // with the collision of collide.cuh (VEL = 1) differentiated by hand below.
 // Misfit J = 1/2 sum_{t in obs} sum_x (phi_t(x) - phi*_t(x))^2, phi_t = sum_i G^t_i,
 // enters the reverse sweep as Gbar^t_i(x) += phi_t(x) - phi*_t(x).

@@ -37,7 +37,8 @@ struct elbm_ctx {
   bool initialized = false;
   double src_amp = 1.0;      // source amplitude of the most recent half-step a_{n-1}
   int lambda_mode = 0;       // 0 closed form, 1 exact root
-  int step_kernel = 0;       // 0 auto, 1 per-node gathers, 2 staged rows
+  int step_kernel = 0;       // 0 auto, 1 per-node gathers, 2 staged rows, 3 pipelined staged rows
+  long long wait_limit = 0;  // staging-wait limit in clock cycles (0: the default, about one second)
   int exact_mass = 1;        // FP32 storage: exact stored node mass
   std::string err;
 };
@@ -468,6 +469,7 @@ elbm_status elbm_step(elbm_handle h, int64_t nsteps) {
   L.kd = &h->kd;
   L.kf = &h->kf;
   L.variant = h->step_kernel;
+  L.wait_limit = h->wait_limit;
   for (int64_t s = 0; s < nsteps; ++s) {
     L.pin = h->pops[h->cur];
     L.sin = h->scale[h->cur];
@@ -488,10 +490,22 @@ elbm_status elbm_set_lambda_mode(elbm_handle h, int32_t mode) {
 }
 
 elbm_status elbm_set_step_kernel(elbm_handle h, int32_t variant) {
-  if (!h || variant < 0 || variant > 2) return fail(h, ELBM_ERR_ARG, "variant must be 0, 1 or 2");
+  if (!h || variant < 0 || variant > 3) return fail(h, ELBM_ERR_ARG, "variant must be 0, 1, 2 or 3");
   if (variant == 2 && !rows_eligible(h->prec, h->nx))
     return fail(h, ELBM_ERR_UNSUPPORTED, "staged-row step needs nx % 8 == 0 and rows that fit in shared memory");
+  if (variant == 3) {
+    const int vel = h->u3 ? 2 : ((h->u[0] != 0.0 || h->u[1] != 0.0 || h->u[2] != 0.0) ? 1 : 0);
+    if (!pipe_eligible(h->prec, h->nx, vel, h->lambda_mode != 0))
+      return fail(h, ELBM_ERR_UNSUPPORTED, "pipelined staged-row step needs nx % 8 == 0 and three row stages "
+                                           "in shared memory");
+  }
   h->step_kernel = variant;
+  return ELBM_OK;
+}
+
+elbm_status elbm_set_wait_limit(elbm_handle h, int64_t cycles) {
+  if (!h || cycles < 0) return fail(h, ELBM_ERR_ARG, "cycles must be >= 0");
+  h->wait_limit = cycles;
   return ELBM_OK;
 }
 

@@ -195,6 +195,16 @@ __global__ void k_batch_read(const DomainInfo* dom, const int* tile_dom, const i
 
 }  // namespace
 
+// An instantiated step sequence, reused while everything it captured is unchanged.
+struct BatchGraph {
+  int mode;
+  int64_t nsteps;
+  int parity, blocks_per_sm, tile, extra, fallback;
+  long long limit;
+  double eps;
+  cudaGraphExec_t exec;
+};
+
 struct elbm_batch_ctx {
   int ndom = 0;
   std::vector<int> edges;
@@ -220,10 +230,41 @@ struct elbm_batch_ctx {
   int fallback = 1;
   bool initialized = false;
   int64_t step = 0;
+  std::vector<BatchGraph> graphs;   // most recently used last
   std::string err;
 };
 
 namespace {
+
+void drop_graphs(elbm_batch_ctx* h) {
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+}
+
+cudaGraphExec_t find_graph(elbm_batch_ctx* h, int mode, int64_t nsteps) {
+  for (size_t i = 0; i < h->graphs.size(); ++i) {
+    const BatchGraph& g = h->graphs[i];
+    if (g.mode == mode && g.nsteps == nsteps && g.parity == h->parity && g.blocks_per_sm == h->blocks_per_sm &&
+        g.tile == h->tile && g.extra == h->extra && g.fallback == h->fallback && g.limit == h->limit &&
+        g.eps == h->eps) {
+      BatchGraph hit = g;
+      h->graphs.erase(h->graphs.begin() + i);
+      h->graphs.push_back(hit);
+      return hit.exec;
+    }
+  }
+  return nullptr;
+}
+
+void keep_graph(elbm_batch_ctx* h, int mode, int64_t nsteps, cudaGraphExec_t exec) {
+  constexpr size_t kMax = 8;
+  if (h->graphs.size() >= kMax) {
+    cudaGraphExecDestroy(h->graphs.front().exec);
+    h->graphs.erase(h->graphs.begin());
+  }
+  h->graphs.push_back(BatchGraph{mode, nsteps, h->parity, h->blocks_per_sm, h->tile, h->extra, h->fallback, h->limit,
+                                 h->eps, exec});
+}
 
 elbm_status bfail(elbm_batch_ctx* h, elbm_status s, const std::string& m) {
   if (h) h->err = m;
@@ -261,6 +302,9 @@ BatchArgs args_of(elbm_batch_ctx* h) {
 }
 
 elbm_status rebuild_tiles(elbm_batch_ctx* h) {
+  // cached graphs hold the tile tables' addresses
+  cudaStreamSynchronize(h->stream);
+  drop_graphs(h);
   std::vector<int> td, tf;
   for (int d = 0; d < h->ndom; ++d) {
     const int N = h->edges[d] * h->edges[d] * h->edges[d];
@@ -365,6 +409,7 @@ elbm_status elbm_batch_create(int32_t ndom, const int32_t* edges, const double* 
 void elbm_batch_destroy(elbm_batch_handle h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  drop_graphs(h);
   cudaFree(h->d_dom);
   cudaFree(h->d_tile_dom);
   cudaFree(h->d_tile_first);
@@ -458,6 +503,14 @@ elbm_status elbm_batch_step(elbm_batch_handle h, int64_t nsteps, int32_t mode) {
     h->step += nsteps;
     return ELBM_OK;
   }
+  // a step sequence captured before with the same shape, state parity and parameters is
+  // relaunched as it is: capture and instantiation stay out of repeated calls
+  if (cudaGraphExec_t cached = find_graph(h, mode, nsteps)) {
+    BCK(cudaGraphLaunch(cached, h->stream), "graph launch");
+    if (nsteps % 2) h->parity ^= 1;
+    h->step += nsteps;
+    return ELBM_OK;
+  }
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   BCK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
@@ -490,10 +543,13 @@ elbm_status elbm_batch_step(elbm_batch_handle h, int64_t nsteps, int32_t mode) {
   }
   if (mode == 0) h->in_graph = 1;
   e = cudaGraphInstantiate(&exec, graph, 0);
-  if (e == cudaSuccess) e = cudaGraphLaunch(exec, h->stream);
-  if (exec) cudaGraphExecDestroy(exec);
   cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return bfail(h, ELBM_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, h->stream);
+  if (e != cudaSuccess) {
+    if (exec) cudaGraphExecDestroy(exec);
+    return bfail(h, ELBM_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  }
+  keep_graph(h, mode, nsteps, exec);
   if (nsteps % 2) h->parity ^= 1;
   h->step += nsteps;
   return ELBM_OK;

@@ -26,7 +26,9 @@ struct StepLaunch {
                                 // as their equilibrium shape, [4..5] row tickets
   const PopConsts<double>* kd;  // host copies, passed by value to the kernel
   const PopConsts<float>* kf;
-  int variant;                  // 0 auto, 1 one thread per node with global gathers, 2 staged rows
+  int variant;                  // 0 auto, 1 one thread per node with global gathers, 2 staged rows,
+                                // 3 staged rows with a producer warp and per-stage full/empty barriers
+  long long wait_limit;         // staging waits of variants 2 and 3 give up after this many cycles
 };
 cudaError_t launch_step(const StepLaunch& L, cudaStream_t s);
 // The implementation launch_step runs (1 per-node, 2 staged rows) for a requested variant
@@ -35,6 +37,9 @@ int step_variant(int prec, int nx, int vel, bool root, int requested);
 // Staged-row kernel (step_rows.cu): usable when rows_eligible(prec, nx); else cudaErrorNotSupported.
 bool rows_eligible(int prec, int nx);
 cudaError_t launch_step_rows(const StepLaunch& L, cudaStream_t s);
+// Pipelined staged-row kernel (step_rows.cu): usable when pipe_eligible(...).
+bool pipe_eligible(int prec, int nx, int vel, bool root);
+cudaError_t launch_step_pipe(const StepLaunch& L, cudaStream_t s);
 
 // State transfer.  mode 0: populations [27][N] <-> caller; mode 1: phi0 [N] -> equilibrium.
 struct StateIO {

@@ -98,7 +98,9 @@ int step_variant(int prec, int nx, int vel, bool root, int requested) {
 
 cudaError_t launch_step(const StepLaunch& L, cudaStream_t s) {
   const bool root = (L.prec == 0 ? L.kd->root : L.kf->root) != 0;
-  if (step_variant(L.prec, L.nx, L.vel, root, L.variant) == 2)
+  const int v = step_variant(L.prec, L.nx, L.vel, root, L.variant);
+  if (v == 3) return launch_step_pipe(L, s);
+  if (v == 2)
     return rows_eligible(L.prec, L.nx) ? launch_step_rows(L, s) : cudaErrorNotSupported;
   switch (L.prec) {
     case 0: return launch_v<double>(L, s);

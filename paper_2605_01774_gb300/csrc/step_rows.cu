@@ -85,7 +85,7 @@ __device__ __forceinline__ void staged_pull(R (&g)[Q], const unsigned char* stag
     for (int i = 0; i < Q; ++i) {
       const int xs = cx_of(i) == 1 ? xm : (cx_of(i) == -1 ? xp : x);
       const float s = S[(i % 9) * W + xs];
-      g[i] = s * fmaf(float(1.0 / (1 << qexp_of(i))), Codec<Elem>::to_f(P[i * W + xs]), k.E[i]);
+      g[i] = s * Codec<Elem>::fma_pow2(P[i * W + xs], qexp_of(i), k.E[i]);
     }
   } else {
 #pragma unroll
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(block_threads(WC), rows_min_blocks<Elem, WC>()
 k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G,
             const typename Storage<Elem>::real* __restrict__ T6, const float* __restrict__ src,
             const float* __restrict__ u3, int fallback, unsigned long long* __restrict__ counters,
-            const PopConsts<typename Storage<Elem>::real> k) {
+            long long wait_limit, const PopConsts<typename Storage<Elem>::real> k) {
   using R = typename Storage<Elem>::real;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[STAGES];
@@ -201,7 +201,7 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
       // ordering of the previous reads of this buffer before the copies: the block barrier
       if (nrow < nrows) issue_row(in, G, W, nrow, smem + sm * SB, &bars[sm]);
     }
-    if (!mbar_wait_bounded(&bars[s], (it / STAGES) & 1, WAIT_LIMIT)) {
+    if (!mbar_wait_bounded(&bars[s], (it / STAGES) & 1, wait_limit)) {
       abort_flag = 1;
     } else {
       const unsigned char* stage = smem + s * SB;
@@ -258,6 +258,199 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// Pipelined variant: one persistent block per SM, a producer warp and NC consumer warps
+// sharing a ring of NS row stages.  Stage s carries two mbarriers: full[s] completes when the
+// producer's bulk copies of a row have landed (transaction count), empty[s] when every consumer
+// lane that worked on that row has arrived.  The unit of consumer work is a 32-node segment of
+// a staged row, taken from a shared counter in row order; a lane releases the stage as soon as
+// its 27 pulled populations are in registers, before the collision, so a warp that meets costly
+// nodes (positivity fallback) holds no stage while it computes and the other warps go on with
+// the next segments; there is no block-wide barrier in the loop.  The producer takes rows
+// from the same global ticket counter as the per-row kernel, waits for empty[s], and refills.
+// When the tickets run out it publishes NS sentinel rows (row index = nrows) so that every
+// consumer, whatever segment it took, sees one and leaves.
+//
+// Correctness conditions (checked on the host, pipe_stages): NC <= NS * nseg, so a consumer can
+// never take a segment of row slot k before slot k - NS has completed (that would need more
+// than NC segments outstanding) -- the parity of full[s] is therefore unambiguous; NS >= 3.
+// The partial per-warp segment (nx % 32 != 0) has idle lanes, which still arrive on empty[s].
+// Consumer warps of the pipelined kernel (one block per SM): FP32 storage, deviation storages.
+#ifndef ELBM_PIPE_NC
+#define ELBM_PIPE_NC 24
+#endif
+#ifndef ELBM_PIPE_NC_DEV
+#define ELBM_PIPE_NC_DEV 19
+#endif
+// Rows handed to a producer per ticket: one global atomic per chunk (the next chunk's ticket
+// is taken one chunk ahead), at the cost of up to a chunk of imbalance at the end of a step.
+#ifndef ELBM_PIPE_CHUNK
+#define ELBM_PIPE_CHUNK 4
+#endif
+constexpr int PIPE_CHUNK = ELBM_PIPE_CHUNK;
+// Resident blocks (independent producer/consumer pipelines) per SM.
+#ifndef ELBM_PIPE_BLOCKS
+#define ELBM_PIPE_BLOCKS 1
+#endif
+constexpr int PIPE_BLOCKS = ELBM_PIPE_BLOCKS;
+constexpr int PIPE_MAX_STAGES = 8;
+constexpr size_t PIPE_SMEM = 200 * 1024 / PIPE_BLOCKS;   // dynamic shared memory of one block's stage ring
+
+template <typename Elem, int VEL, bool ROOT>
+__host__ __device__ constexpr int pipe_consumer_warps() {
+  return std::is_same<Elem, double>::value ? 12
+                                            : ((VEL == 2 || ROOT) ? 16 : (Storage<Elem>::dev ? ELBM_PIPE_NC_DEV : ELBM_PIPE_NC));
+}
+
+template <typename Elem, int VEL, bool ROOT>
+__host__ __device__ constexpr int pipe_threads() {
+  return 32 * (pipe_consumer_warps<Elem, VEL, ROOT>() + 1);
+}
+
+template <typename Elem, int VEL, bool ROOT, int WC>
+__global__ void __launch_bounds__(pipe_threads<Elem, VEL, ROOT>(), PIPE_BLOCKS)
+k_step_pipe(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G,
+            const typename Storage<Elem>::real* __restrict__ T6, const float* __restrict__ src,
+            const float* __restrict__ u3, int fallback, unsigned long long* __restrict__ counters,
+            long long wait_limit, int NS, const PopConsts<typename Storage<Elem>::real> k) {
+  using R = typename Storage<Elem>::real;
+  constexpr int NC = pipe_consumer_warps<Elem, VEL, ROOT>();
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t full[PIPE_MAX_STAGES], empty[PIPE_MAX_STAGES];
+  __shared__ int s_row[PIPE_MAX_STAGES];
+  __shared__ int s_item;
+  __shared__ int abort_flag;
+  const int W = WC > 0 ? WC : G.nx;
+  const int nseg = (W + 31) >> 5;
+  const size_t SB = stage_bytes<Elem>(W);
+  const int nrows = G.ny * G.nz;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < NS; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&empty[b], 32 * nseg);
+    }
+    mbar_fence_init();
+    s_item = 0;
+    abort_flag = 0;
+  }
+  __syncthreads();
+  volatile int* vabort = &abort_flag;
+
+  if (warp == NC) {
+    // ---- producer warp
+    bool exhausted = false, aborted = false;
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(counters + TICKET, (unsigned long long)PIPE_CHUNK);   // next chunk
+    int kk = 0, k_real = 0, sentinels = 0, next_row = 0, left = 0;
+    for (; sentinels < NS; ++kk) {
+      const int s = kk % NS;
+      int row = nrows;
+      if (!exhausted && left == 0) {
+        const unsigned long long tt = __shfl_sync(0xffffffffu, t, 0);
+        if (tt < (unsigned long long)nrows) {
+          next_row = (int)tt;
+          left = min(PIPE_CHUNK, nrows - next_row);
+          if (lane == 0) t = atomicAdd(counters + TICKET, (unsigned long long)PIPE_CHUNK);  // overlaps the rows
+        } else {
+          exhausted = true;
+        }
+      }
+      if (!exhausted) {
+        row = next_row++;
+        --left;
+      }
+      // stage s was last used by slot kk - NS: every consumer lane of that row must have left it
+      if (kk >= NS && !mbar_wait_or_abort(&empty[s], ((kk / NS) - 1) & 1, wait_limit, vabort)) {
+        aborted = true;
+        break;
+      }
+      if (*vabort) {
+        aborted = true;
+        break;
+      }
+      if (lane == 0) s_row[s] = row;             // released by the arrival on full[s]
+      if (row < nrows) {
+        issue_row(in, G, W, row, smem + s * SB, &full[s]);
+        k_real = kk + 1;
+      } else {
+        if (lane == 0) mbar_arrive(&full[s]);
+        ++sentinels;
+      }
+    }
+    if (aborted) {
+      if (lane == 0) {
+        *vabort = 1;
+        atomicExch(counters + 2, 1ull);
+      }
+      // no copy may still be writing this block's shared memory when it exits: wait (bounded,
+      // full limit) for the row slots issued last whose stages were never refilled
+      for (int m = kk - NS > 0 ? kk - NS : 0; m < k_real; ++m)
+        mbar_wait_bounded(&full[m % NS], (m / NS) & 1, WAIT_LIMIT);
+    }
+    if (lane == 0) {
+      // this block takes no more tickets; the last block to finish resets the scheduler
+      __threadfence();
+      if (atomicAdd(counters + DONE, 1ull) == (unsigned long long)gridDim.x - 1) {
+        atomicExch(counters + TICKET, 0ull);
+        atomicExch(counters + DONE, 0ull);
+      }
+    }
+    return;
+  }
+
+  // ---- consumer warps
+  unsigned took = 0, proj = 0;
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(&s_item, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    const int slot = it / nseg, q = it - slot * nseg, s = slot % NS;
+    if (!mbar_wait_or_abort(&full[s], (slot / NS) & 1, wait_limit, vabort)) {
+      if (lane == 0 && atomicExch(&abort_flag, 1) == 0) atomicExch(counters + 2, 1ull);
+      break;
+    }
+    const int row = *(volatile int*)&s_row[s];
+    if (row >= nrows) break;
+    const int x = (q << 5) + lane;
+    R g[Q];
+    if (x < W) staged_pull<Elem, R>(g, smem + s * SB, W, x, k);
+    // the lane's populations are in registers: release the stage before the collision, so a
+    // slow segment holds its stage only for its loads (the arrival orders them before any
+    // later copy into the stage)
+    mbar_arrive(&empty[s]);
+    if (x < W) {
+      const int n = row * W + x;
+      if (G.dirichlet) abb_faces<Elem, R>(g, in, G, x, n, k);
+      if (src != nullptr) {
+        // merged Strang half-steps of consecutive steps (Section 3.3)
+        const R r = k.src_step * R(__ldg(src + n));
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] += r * k.E[i];
+      }
+      const Sym6<R> T = load_T<R>(T6, G.N, n, k.T);
+      R phi;
+      bool tk;
+      if constexpr (VEL == 2) {
+        const R un[3] = {R(__ldg(u3 + n)), R(__ldg(u3 + G.N + n)), R(__ldg(u3 + 2 * G.N + n))};
+        tk = collide_node<R, 2, ROOT>(g, T, k, fallback != 0, phi, un);
+      } else {
+        tk = collide_node<R, VEL, ROOT>(g, T, k, fallback != 0, phi);
+      }
+      took += tk ? 1u : 0u;
+      proj += Storage<Elem>::store(pout, sout, (int)G.N, n, g, k.Ek, phi, k.exact_mass != 0) ? 1u : 0u;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) took += __shfl_xor_sync(0xffffffffu, took, o);
+  if (took != 0u && lane == 0) atomicAdd(counters, (unsigned long long)took);
+  if constexpr (Storage<Elem>::dev) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) proj += __shfl_xor_sync(0xffffffffu, proj, o);
+    if (proj != 0u && lane == 0) atomicAdd(counters + 3, (unsigned long long)proj);
+  }
+}
+
 namespace {
 
 // Blocks of k_step_rows<Elem, VEL, ROOT, WC> resident per SM at row length W (0: not
@@ -299,7 +492,8 @@ cudaError_t launch_rows_t(const StepLaunch& L, cudaStream_t s) {
   const PopConsts<R>& k = *reinterpret_cast<const PopConsts<R>*>(std::is_same<R, double>::value ? (const void*)L.kd
                                                                                                : (const void*)L.kf);
   k_step_rows<Elem, VEL, ROOT, WC><<<grid, block_threads(WC), STAGES * stage_bytes<Elem>(L.nx), s>>>(
-      in, static_cast<Elem*>(L.pout), L.sout, G, static_cast<const R*>(L.T6), L.src, L.u3, L.fallback, L.counters, k);
+      in, static_cast<Elem*>(L.pout), L.sout, G, static_cast<const R*>(L.T6), L.src, L.u3, L.fallback, L.counters,
+      L.wait_limit > 0 ? L.wait_limit : WAIT_LIMIT, k);
   return cudaGetLastError();
 }
 
@@ -316,6 +510,87 @@ cudaError_t launch_rows_v(const StepLaunch& L, cudaStream_t s) {
 }
 
 }  // namespace
+
+// ---- pipelined variant: launch configuration
+
+namespace {
+
+// Stages of the pipelined kernel for storage `prec` at row length W (0: not available):
+// as many as fit in PIPE_SMEM, at most PIPE_MAX_STAGES, at least 3, and enough that the NC
+// consumer warps can never reach a stage two uses ahead (NC <= NS * nseg).
+int pipe_stages_for(int prec, int W, int nc) {
+  if (W < 8 || W % 8 != 0) return 0;
+  const size_t e = prec == 0 ? 8 : (prec == 1 ? 4 : 2);
+  const size_t sb = stage_bytes_for(W, e, prec >= 2);
+  const int ns = (int)std::min<size_t>(PIPE_MAX_STAGES, PIPE_SMEM / sb);
+  const int nseg = (W + 31) / 32;
+  if (ns < 3 || nc > ns * nseg) return 0;
+  return ns;
+}
+
+template <typename Elem, int VEL, bool ROOT, int WC>
+cudaError_t launch_pipe_t(const StepLaunch& L, cudaStream_t s) {
+  using R = typename Storage<Elem>::real;
+  constexpr int NC = pipe_consumer_warps<Elem, VEL, ROOT>();
+  const int ns = pipe_stages_for(L.prec, L.nx, NC);
+  if (ns == 0) return cudaErrorNotSupported;
+  const size_t dyn = (size_t)ns * stage_bytes<Elem>(L.nx);
+  static int c_dev = -1;
+  static size_t c_dyn = 0;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  if (dev != c_dev || dyn > c_dyn) {
+    cudaError_t e = cudaFuncSetAttribute(k_step_pipe<Elem, VEL, ROOT, WC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    c_dev = dev;
+    c_dyn = dyn;
+  }
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long nrows = (long long)L.ny * L.nz;
+  const int grid = (int)std::min<long long>(nrows, (long long)PIPE_BLOCKS * nsm);
+  Field<Elem> in{static_cast<const Elem*>(L.pin), L.sin};
+  Grid G{L.nx, L.ny, L.nz, L.N, L.dirichlet};
+  const PopConsts<R>& k = *reinterpret_cast<const PopConsts<R>*>(std::is_same<R, double>::value ? (const void*)L.kd
+                                                                                               : (const void*)L.kf);
+  k_step_pipe<Elem, VEL, ROOT, WC><<<grid, pipe_threads<Elem, VEL, ROOT>(), dyn, s>>>(
+      in, static_cast<Elem*>(L.pout), L.sout, G, static_cast<const R*>(L.T6), L.src, L.u3, L.fallback, L.counters,
+      L.wait_limit > 0 ? L.wait_limit : WAIT_LIMIT, ns, k);
+  return cudaGetLastError();
+}
+
+template <typename Elem>
+cudaError_t launch_pipe_v(const StepLaunch& L, cudaStream_t s) {
+  const bool root = (std::is_same<Elem, double>::value ? L.kd->root : L.kf->root) != 0;
+  if (L.vel == 2) return root ? launch_pipe_t<Elem, 2, true, 0>(L, s) : launch_pipe_t<Elem, 2, false, 0>(L, s);
+  if (root) return L.vel == 1 ? launch_pipe_t<Elem, 1, true, 0>(L, s) : launch_pipe_t<Elem, 0, false, 0>(L, s);
+  // closed-form stabilizer, uniform velocity: row lengths 256, 384 and 512 compiled in
+  if (L.nx == 256) return L.vel == 1 ? launch_pipe_t<Elem, 1, false, 256>(L, s) : launch_pipe_t<Elem, 0, false, 256>(L, s);
+  if (L.nx == 512) return L.vel == 1 ? launch_pipe_t<Elem, 1, false, 512>(L, s) : launch_pipe_t<Elem, 0, false, 512>(L, s);
+  if (L.nx == 384) return L.vel == 1 ? launch_pipe_t<Elem, 1, false, 384>(L, s) : launch_pipe_t<Elem, 0, false, 384>(L, s);
+  return L.vel == 1 ? launch_pipe_t<Elem, 1, false, 0>(L, s) : launch_pipe_t<Elem, 0, false, 0>(L, s);
+}
+
+}  // namespace
+
+bool pipe_eligible(int prec, int nx, int vel, bool root) {
+  int nc = prec >= 2 ? ELBM_PIPE_NC_DEV : ELBM_PIPE_NC;
+  if (prec == 0) nc = 12;
+  else if (vel == 2 || root) nc = 16;
+  return pipe_stages_for(prec, nx, nc) > 0;
+}
+
+cudaError_t launch_step_pipe(const StepLaunch& L, cudaStream_t s) {
+  const bool root = (L.prec == 0 ? L.kd->root : L.kf->root) != 0;
+  if (!pipe_eligible(L.prec, L.nx, L.vel, root)) return cudaErrorNotSupported;
+  switch (L.prec) {
+    case 0: return launch_pipe_v<double>(L, s);
+    case 1: return launch_pipe_v<float>(L, s);
+    case 2: return launch_pipe_v<__half>(L, s);
+    case 3: return launch_pipe_v<__nv_bfloat16>(L, s);
+  }
+  return cudaErrorInvalidValue;
+}
 
 // Shared memory of all staging buffers within 200 KiB; rows of 16-byte multiples.
 bool rows_eligible(int prec, int nx) {

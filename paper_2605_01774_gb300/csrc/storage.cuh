@@ -26,6 +26,14 @@ struct Codec;
 template <>
 struct Codec<__half> {
   static __device__ __forceinline__ float to_f(__half h) { return __half2float(h); }
+  // 2^-e v + c with one rounding (mixed-precision FMA: the FP16 operand enters unconverted and
+  // the product with the exact power of two is exact), e.g. the decode E_i + 2^-e_i v_i
+  static __device__ __forceinline__ float fma_pow2(__half v, int e, float c) {
+    float r;
+    asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(r) : "h"(__half_as_ushort(v)), "h"((unsigned short)((15 - e) << 10)),
+        "f"(c));
+    return r;
+  }
   static __device__ __forceinline__ __half from_f(float f) {
     unsigned short h;
     asm("cvt.rn.satfinite.f16.f32 %0, %1;" : "=h"(h) : "f"(f));
@@ -35,6 +43,12 @@ struct Codec<__half> {
 template <>
 struct Codec<__nv_bfloat16> {
   static __device__ __forceinline__ float to_f(__nv_bfloat16 h) { return __bfloat162float(h); }
+  static __device__ __forceinline__ float fma_pow2(__nv_bfloat16 v, int e, float c) {
+    float r;
+    asm("fma.rn.f32.bf16 %0, %1, %2, %3;" : "=f"(r) : "h"(__bfloat16_as_ushort(v)),
+        "h"((unsigned short)((127 - e) << 7)), "f"(c));
+    return r;
+  }
   static __device__ __forceinline__ __nv_bfloat16 from_f(float f) { return __float2bfloat16_rn(f); }
 };
 
@@ -53,7 +67,7 @@ struct Storage {
     const Elem v = __ldg(pops + (i * N + src));  // 27 N < 2^31 is checked at creation
     if constexpr (dev) {
       const float s = __ldg(scale + src);
-      return s * fmaf(float(1.0 / (1 << qexp_of(i))), Codec<Elem>::to_f(v), E_i);
+      return s * Codec<Elem>::fma_pow2(v, qexp_of(i), E_i);
     } else {
       return v;
     }
@@ -84,7 +98,7 @@ struct Storage {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
           const Elem q = Codec<Elem>::from_f(fmaf(a[i], ik[nnz_of(i)], -Ek[i]));
-          s = fmaf(float(1.0 / (1 << qexp_of(i))), Codec<Elem>::to_f(q), s);
+          s = Codec<Elem>::fma_pow2(q, qexp_of(i), s);
           pops[i * N + n] = q;
         }
         if (!(fabsf(s) >= 0.5f)) {          // NaN stays on this path and stays visible

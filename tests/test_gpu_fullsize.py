@@ -5,9 +5,19 @@ source nodes of each sampled node are collided in FP64 and streamed).
 
 Tolerances per form: FP32 1e-6 relative L2 over the sampled populations; FP16
 deviations 2e-4 and BF16 deviations 2e-3 (storage unit 4.9e-4 / 3.9e-3 on
-relative deviations of order 1e-1).  Nodes where the FP32 and FP64 sides take a
-different branch of the stabilizer guard or the positivity fallback are
-threshold crossings; they are counted and must stay below 1% of the samples.
+relative deviations of order 1e-1); no sample may exceed 50x that per node.
+
+A sample is excused from these bounds only where the oracle shows that one of the
+collisions feeding it sits at a threshold that FP32 arithmetic can resolve either way:
+the stabilizer guard <dh|dh>_H = theta^2 phi within 1 % (u != 0 only), the positivity
+fallback min_i (g_i + Omega_i) within 1e-5 of the node's largest population of 0, or a
+far-tail node with phi < 1e-25 (FP32 flush-to-zero and the phi > 1e-30 guard).  Excused
+samples are counted (below 5 %) and their error is capped at max(1e-3, 50 tol): a guard
+crossing moves a population by kappa dh ~ theta phi.
+
+Besides random samples, every node of four boundary lines is sampled (x = 0, x = Nx - 1,
+y = 0 and z = Nz - 1), so a wrong periodic wrap or anti-bounce-back face in the staged-row
+kernels shows on hundreds of samples.
 """
 import numpy as np
 import pytest
@@ -34,7 +44,39 @@ def _sample_nodes(dims, m, seed):
     nx, ny, nz = dims
     pts = np.stack([rng.integers(0, nx, m), rng.integers(0, ny, m), rng.integers(0, nz, m)], 1)
     edges = np.array([[0, 0, 0], [nx - 1, ny - 1, nz - 1], [0, ny // 2, nz - 1], [nx - 1, 0, nz // 2]])
-    return np.concatenate([pts, edges])
+    return np.concatenate([pts, edges, _boundary_lines(dims, seed)])
+
+
+def _boundary_lines(dims, seed):
+    """Every node of the lines (x = 0, y0, z0), (x = Nx - 1, y1, z1) along y, and of the lines
+    y = 0 and z = Nz - 1 along x: the periodic wraps in y and z and the x faces."""
+    rng = np.random.default_rng(seed + 100)
+    nx, ny, nz = dims
+    y0, z0, y1, z1 = (int(v) for v in rng.integers(0, min(ny, nz), 4))
+    a = np.stack([np.zeros(ny, int), np.arange(ny), np.full(ny, z0)], 1)
+    b = np.stack([np.full(ny, nx - 1), np.arange(ny), np.full(ny, z1)], 1)
+    c = np.stack([np.arange(nx), np.zeros(nx, int), np.full(nx, y0 % nz)], 1)
+    d = np.stack([np.arange(nx), np.full(nx, y1 % ny), np.full(nx, nz - 1)], 1)
+    return np.concatenate([a, b, c, d])
+
+
+def _threshold_nodes(g, u, S, theta):
+    """Per collision: True where FP32 arithmetic can legitimately take the other branch of the
+    stabilizer guard or of the positivity fallback, or where phi is in the far tail."""
+    phi = g.sum(0)
+    geq = O.equilibrium(phi, u)
+    gneq = g - geq
+    dh = gneq - O.lift(O.first_moment(gneq))
+    ok = (geq > 0).all(0) & (phi > 0)
+    hh = torch.where(ok, (dh * dh / torch.where(geq > 0, geq, torch.ones_like(geq))).sum(0), torch.zeros_like(phi))
+    guard = torch.zeros_like(phi, dtype=torch.bool)
+    if bool((u != 0).any()):
+        guard = ok & ((hh / (theta * theta * torch.where(phi > 0, phi, torch.ones_like(phi))) - 1.0).abs() < 1e-2)
+    post, _ = O.collide(g, u, S, theta=theta, lam_mode="reduced", fallback=False)
+    scale = g.abs().max(0).values
+    fb = post.min(0).values.abs() <= 1e-5 * scale
+    tail = phi.abs() < 1e-25
+    return guard | fb | tail
 
 
 def _oracle_one_step(g_prev, dims, pts, u, S_of, theta, bc=None, src=None):
@@ -59,6 +101,7 @@ def _oracle_one_step(g_prev, dims, pts, u, S_of, theta, bc=None, src=None):
         gsrc = O.source_half_step(gsrc, R, u)
     S = S_of(fx, fy, fz)
     gpost, info = O.collide(gsrc, u, S, theta=theta, lam_mode="reduced")
+    excusable = _threshold_nodes(gsrc, u, S, theta).view(27, m).any(0)
     out = torch.empty(27, m, dtype=torch.float64)
     gp = gpost.view(27, 27, m)                                              # [pop, source-of-pop, sample]
     for i in range(27):
@@ -73,6 +116,7 @@ def _oracle_one_step(g_prev, dims, pts, u, S_of, theta, bc=None, src=None):
             gown = O.source_half_step(gown, Ro, u)
         Sown = S_of(pts[:, 0], pts[:, 1], pts[:, 2])
         gpo, _ = O.collide(gown, u, Sown, theta=theta, lam_mode="reduced")
+        excusable = excusable | _threshold_nodes(gown, u, Sown, theta)
         for i in range(27):
             if o[i].any():
                 cx = C[i][0]
@@ -81,7 +125,7 @@ def _oracle_one_step(g_prev, dims, pts, u, S_of, theta, bc=None, src=None):
     if src is not None:
         R = torch.as_tensor(src.reshape(-1)[pts[:, 0] + nx * (pts[:, 1] + ny * pts[:, 2])])
         out = O.source_half_step(out, R, u)
-    return out, info
+    return out, excusable
 
 
 def _gpu_at(g, dims, pts):
@@ -90,19 +134,23 @@ def _gpu_at(g, dims, pts):
     return g.reshape(27, -1)[:, idx].double().cpu()
 
 
-def _compare(name, gpu, ref, tol):
+def _compare(name, gpu, ref, tol, excusable):
     # per-node error relative to the node's own size, with an absolute floor of 1e-6 of the
-    # largest sampled node: far-tail nodes (phi down to 1e-38) are compared in absolute terms,
-    # where FP32 flush-to-zero and the phi > 1e-30 stabilizer guard legitimately differ
+    # largest sampled node (far-tail nodes, phi down to 1e-38, are compared in absolute terms)
     nrm = torch.linalg.vector_norm(ref, dim=0)
     floor = 1e-6 * nrm.max()
     per_node = torch.linalg.vector_norm(gpu - ref, dim=0) / torch.maximum(nrm, floor)
-    bad = (per_node > 50 * tol).float().mean().item()
-    good = per_node <= 50 * tol
-    rel = (torch.linalg.vector_norm((gpu - ref)[:, good]) / torch.linalg.vector_norm(ref[:, good])).item()
-    print(f"{name}: sampled rel L2 {rel:.2e}, threshold-crossing fraction {bad:.4f}")
+    keep = ~excusable
+    rel = (torch.linalg.vector_norm((gpu - ref)[:, keep]) / torch.linalg.vector_norm(ref[:, keep])).item()
+    worst_kept = per_node[keep].max().item()
+    worst_excused = per_node[excusable].max().item() if bool(excusable.any()) else 0.0
+    frac = excusable.float().mean().item()
+    print(f"{name}: sampled rel L2 {rel:.2e}, worst node {worst_kept:.2e}; threshold samples {frac:.4f} "
+          f"(worst {worst_excused:.2e})")
     assert rel < tol, (name, rel)
-    assert bad < 0.01, (name, bad)
+    assert worst_kept < 50 * tol, (name, worst_kept)
+    assert frac < 0.05, (name, frac)
+    assert worst_excused < max(1e-3, 50 * tol), (name, worst_excused)
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16dev", "bf16dev"])
@@ -124,8 +172,8 @@ def test_plume_256_sampled(E, prec):
     pts = np.concatenate([_sample_nodes(wl.dims, 1500, 1),
                           (np.asarray(wl.meta["mu0"]) + np.random.default_rng(2).normal(0, 10, (1500, 3))).astype(int) % 256])
     S = O.relaxation_matrix(torch.as_tensor(wl.D))
-    ref, _ = _oracle_one_step(g0, wl.dims, pts, torch.as_tensor(wl.u), lambda x, y, z: S, 3e-4)
-    _compare(f"plume256 {prec}", _gpu_at(g1, wl.dims, pts), ref, TOL[prec])
+    ref, exc = _oracle_one_step(g0, wl.dims, pts, torch.as_tensor(wl.u), lambda x, y, z: S, 3e-4)
+    _compare(f"plume256 {prec}", _gpu_at(g1, wl.dims, pts), ref, TOL[prec], exc)
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16dev"])
@@ -150,9 +198,9 @@ def test_heterogeneous_384_sampled(E, prec):
         D = synth.matrix_from_d6(np.moveaxis(D6f[:, z, y, x], 0, -1))
         return O.relaxation_matrix(torch.as_tensor(D))
     src = wl.source.astype(np.float32).astype(np.float64)
-    ref, _ = _oracle_one_step(g0, wl.dims, pts, torch.zeros(3, dtype=torch.float64), S_of, 3e-4,
-                              bc=wl.dirichlet_x, src=src)
-    _compare(f"heterogeneous384 {prec}", _gpu_at(g1, wl.dims, pts), ref, TOL[prec])
+    ref, exc = _oracle_one_step(g0, wl.dims, pts, torch.zeros(3, dtype=torch.float64), S_of, 3e-4,
+                                bc=wl.dirichlet_x, src=src)
+    _compare(f"heterogeneous384 {prec}", _gpu_at(g1, wl.dims, pts), ref, TOL[prec], exc)
 
 
 def test_plume_256_long_run_deviation_forms(E):
