@@ -214,10 +214,30 @@ __device__ __forceinline__ bool collide_node(R (&g)[Q], const Sym6<R>& T, const 
   }
   bool took = false;
   if (fallback) {
-    R mn = gs[0];
+    bool any = false;
+    bool scanned = false;
+    if constexpr (sizeof(R) == 8) {
+      if (k.eps == R(0)) {
+        // FP64 with eps = 0: some g*_i < 0, read from the bit patterns (sign bit set and not
+        // -0), so that the test takes integer instructions instead of FP64-pipe compares
+        unsigned neg = 0u;
 #pragma unroll
-    for (int i = 1; i < Q; ++i) mn = mn < gs[i] ? mn : gs[i];
-    if (mn < k.eps) {
+        for (int i = 0; i < Q; ++i) {
+          const int hi = __double2hiint(gs[i]);
+          const unsigned mag = (unsigned)(hi << 1) | (unsigned)__double2loint(gs[i]);
+          neg |= (unsigned)(hi < 0) & (unsigned)(mag != 0u);
+        }
+        any = neg != 0u;
+        scanned = true;
+      }
+    }
+    if (!scanned) {
+      R mn = gs[0];
+#pragma unroll
+      for (int i = 1; i < Q; ++i) mn = mn < gs[i] ? mn : gs[i];
+      any = mn < k.eps;
+    }
+    if (any) {
       took = true;
       // alpha = min over Omega_i < 0 of (g_i - eps) / (-Omega_i), capped at 1.  A ratio is
       // below 1 exactly when g_i + Omega_i < eps, so only the violating populations need a

@@ -259,8 +259,8 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
 }
 
 // ------------------------------------------------------------------------------------------
-// Pipelined variant: one persistent block per SM, a producer warp and NC consumer warps
-// sharing a ring of NS row stages.  Stage s carries two mbarriers: full[s] completes when the
+// Pipelined variant: persistent blocks (two per SM, one for FP64), each a producer warp and NC
+// consumer warps sharing a ring of NS row stages.  Stage s carries two mbarriers: full[s] completes when the
 // producer's bulk copies of a row have landed (transaction count), empty[s] when every consumer
 // lane that worked on that row has arrived.  The unit of consumer work is a 32-node segment of
 // a staged row, taken from a shared counter in row order; a lane releases the stage as soon as
@@ -275,12 +275,13 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
 // never take a segment of row slot k before slot k - NS has completed (that would need more
 // than NC segments outstanding) -- the parity of full[s] is therefore unambiguous; NS >= 3.
 // The partial per-warp segment (nx % 32 != 0) has idle lanes, which still arrive on empty[s].
-// Consumer warps of the pipelined kernel (one block per SM): FP32 storage, deviation storages.
+// Consumer warps per block of the pipelined kernel: FP32 storage, deviation storages (two
+// blocks per SM: 2 x 12 warps at 80 registers, 2 x 10 warps at 96 registers).
 #ifndef ELBM_PIPE_NC
-#define ELBM_PIPE_NC 24
+#define ELBM_PIPE_NC 11
 #endif
 #ifndef ELBM_PIPE_NC_DEV
-#define ELBM_PIPE_NC_DEV 19
+#define ELBM_PIPE_NC_DEV 9
 #endif
 // Rows handed to a producer per ticket: one global atomic per chunk (the next chunk's ticket
 // is taken one chunk ahead), at the cost of up to a chunk of imbalance at the end of a step.
@@ -288,18 +289,29 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
 #define ELBM_PIPE_CHUNK 4
 #endif
 constexpr int PIPE_CHUNK = ELBM_PIPE_CHUNK;
-// Resident blocks (independent producer/consumer pipelines) per SM.
+// Resident blocks (independent producer/consumer pipelines) per SM for the FP32-arithmetic
+// storages; FP64 runs one.  Measured on the 256^3 plume: one pipeline per SM is limited by the
+// rate at which its single producer warp takes rows and issues their copies (FP32 0.71-0.79
+// ms/step against 0.52-0.58 for the per-row kernel); two pipelines match the per-row kernel.
 #ifndef ELBM_PIPE_BLOCKS
-#define ELBM_PIPE_BLOCKS 1
+#define ELBM_PIPE_BLOCKS 2
 #endif
-constexpr int PIPE_BLOCKS = ELBM_PIPE_BLOCKS;
 constexpr int PIPE_MAX_STAGES = 8;
-constexpr size_t PIPE_SMEM = 200 * 1024 / PIPE_BLOCKS;   // dynamic shared memory of one block's stage ring
+#ifndef ELBM_PIPE_SMEM_KB
+#define ELBM_PIPE_SMEM_KB 200
+#endif
+constexpr size_t PIPE_SMEM_SM = ELBM_PIPE_SMEM_KB * 1024;   // stage rings of all blocks of an SM
+
+__host__ __device__ constexpr int pipe_blocks_for(int prec) { return prec == 0 ? 1 : ELBM_PIPE_BLOCKS; }
+template <typename Elem>
+__host__ __device__ constexpr int pipe_blocks() {
+  return std::is_same<Elem, double>::value ? 1 : ELBM_PIPE_BLOCKS;
+}
 
 template <typename Elem, int VEL, bool ROOT>
 __host__ __device__ constexpr int pipe_consumer_warps() {
   return std::is_same<Elem, double>::value ? 12
-                                            : ((VEL == 2 || ROOT) ? 16 : (Storage<Elem>::dev ? ELBM_PIPE_NC_DEV : ELBM_PIPE_NC));
+                                            : ((VEL == 2 || ROOT) ? 7 : (Storage<Elem>::dev ? ELBM_PIPE_NC_DEV : ELBM_PIPE_NC));
 }
 
 template <typename Elem, int VEL, bool ROOT>
@@ -308,7 +320,7 @@ __host__ __device__ constexpr int pipe_threads() {
 }
 
 template <typename Elem, int VEL, bool ROOT, int WC>
-__global__ void __launch_bounds__(pipe_threads<Elem, VEL, ROOT>(), PIPE_BLOCKS)
+__global__ void __launch_bounds__(pipe_threads<Elem, VEL, ROOT>(), pipe_blocks<Elem>())
 k_step_pipe(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G,
             const typename Storage<Elem>::real* __restrict__ T6, const float* __restrict__ src,
             const float* __restrict__ u3, int fallback, unsigned long long* __restrict__ counters,
@@ -522,7 +534,7 @@ int pipe_stages_for(int prec, int W, int nc) {
   if (W < 8 || W % 8 != 0) return 0;
   const size_t e = prec == 0 ? 8 : (prec == 1 ? 4 : 2);
   const size_t sb = stage_bytes_for(W, e, prec >= 2);
-  const int ns = (int)std::min<size_t>(PIPE_MAX_STAGES, PIPE_SMEM / sb);
+  const int ns = (int)std::min<size_t>(PIPE_MAX_STAGES, PIPE_SMEM_SM / pipe_blocks_for(prec) / sb);
   const int nseg = (W + 31) / 32;
   if (ns < 3 || nc > ns * nseg) return 0;
   return ns;
@@ -548,7 +560,7 @@ cudaError_t launch_pipe_t(const StepLaunch& L, cudaStream_t s) {
   }
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const long long nrows = (long long)L.ny * L.nz;
-  const int grid = (int)std::min<long long>(nrows, (long long)PIPE_BLOCKS * nsm);
+  const int grid = (int)std::min<long long>(nrows, (long long)pipe_blocks<Elem>() * nsm);
   Field<Elem> in{static_cast<const Elem*>(L.pin), L.sin};
   Grid G{L.nx, L.ny, L.nz, L.N, L.dirichlet};
   const PopConsts<R>& k = *reinterpret_cast<const PopConsts<R>*>(std::is_same<R, double>::value ? (const void*)L.kd
@@ -576,7 +588,7 @@ cudaError_t launch_pipe_v(const StepLaunch& L, cudaStream_t s) {
 bool pipe_eligible(int prec, int nx, int vel, bool root) {
   int nc = prec >= 2 ? ELBM_PIPE_NC_DEV : ELBM_PIPE_NC;
   if (prec == 0) nc = 12;
-  else if (vel == 2 || root) nc = 16;
+  else if (vel == 2 || root) nc = 7;
   return pipe_stages_for(prec, nx, nc) > 0;
 }
 

@@ -204,20 +204,17 @@ def heterogeneous(n=384, seed=3, steps=50, porosity=0.6, src_amp=1e-4, src_width
                                                        + kr[2] * z / dims[2]) + pr))
     a, b, c = ang
     ca, sa, cb, sb, cc, sc = np.cos(a), np.sin(a), np.cos(b), np.sin(b), np.cos(c), np.sin(c)
-    # R = Rz(a) Ry(b) Rz(c), written out per node
-    R = np.empty(dims[::-1] + (3, 3))
-    R[..., 0, 0] = ca * cb * cc - sa * sc
-    R[..., 0, 1] = -ca * cb * sc - sa * cc
-    R[..., 0, 2] = ca * sb
-    R[..., 1, 0] = sa * cb * cc + ca * sc
-    R[..., 1, 1] = -sa * cb * sc + ca * cc
-    R[..., 1, 2] = sa * sb
-    R[..., 2, 0] = -sb * cc
-    R[..., 2, 1] = sb * sc
-    R[..., 2, 2] = cb
-    lam = np.where(mask[..., None], np.asarray(PORE_EIG), np.asarray(SOLID_EIG))
-    D = np.einsum("...ak,...k,...bk->...ab", R, lam, R)
-    D6 = np.moveaxis(d6_from_matrix(D), -1, 0).copy()
+    del ang, a, b, c
+    # R = Rz(a) Ry(b) Rz(c), written out per node as its nine entries R[r][k]
+    R = [[ca * cb * cc - sa * sc, -ca * cb * sc - sa * cc, ca * sb],
+         [sa * cb * cc + ca * sc, -sa * cb * sc + ca * cc, sa * sb],
+         [-sb * cc, sb * sc, cb]]
+    lam = [np.where(mask, PORE_EIG[k], SOLID_EIG[k]) for k in range(3)]
+    # D = R diag(lam) R^T, the six components (xx, xy, xz, yy, yz, zz)
+    D6 = np.empty((6,) + dims[::-1])
+    for q, (r1, r2) in enumerate(((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))):
+        D6[q] = R[r1][0] * lam[0] * R[r2][0] + R[r1][1] * lam[1] * R[r2][1] + R[r1][2] * lam[2] * R[r2][2]
+    del R, lam
     mu = tuple((d - 1) / 2.0 for d in dims)
     src = gaussian(dims, mu, src_width, peak=src_amp)
     # linear initial profile between the two Dirichlet values
