@@ -611,6 +611,21 @@ def oracle_sample(n=40):
 
 
 def cpu_model() -> str:
+    """Host CPU model: lscpu's model name (Arm hosts report the core, e.g. Neoverse-V2), else
+    /proc/cpuinfo's, else the machine type; with the vendor where lscpu gives one."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        info = {}
+        for line in out.splitlines():
+            if ":" in line:
+                k, v = line.split(":", 1)
+                info.setdefault(k.strip().lower(), v.strip())
+        if info.get("model name"):
+            vendor = info.get("vendor id", "")
+            return (vendor + " " if vendor and vendor not in info["model name"] else "") + info["model name"]
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         for line in open("/proc/cpuinfo"):
             key = line.split(":")[0].strip().lower()
@@ -618,7 +633,6 @@ def cpu_model() -> str:
                 return line.split(":", 1)[1].strip()
     except OSError:
         pass
-    import platform
     return platform.processor() or platform.machine()
 
 
