@@ -127,10 +127,12 @@ __device__ __forceinline__ void node_tables(PopConsts<R>& kn, R ux, R uy, R uz) 
   for (int i = 0; i < Q; ++i) {
     const R cu = R(cx_of(i)) * ux + R(cy_of(i)) * uy + R(cz_of(i)) * uz;
     const R P = R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu;
+    // one reciprocal per population serves both quotients (correctly rounded in FP32)
+    const R rP = sizeof(R) == 4 ? R(__frcp_rn(float(P))) : R(1) / P;
     kn.E[i] = R(w_of(i)) * P;
-    kn.K3[i] = R(3) * (R(1) / P - R(1));
+    kn.K3[i] = R(3) * (rP - R(1));
     kn.L[i] = log(P) - R(3) * cu + R(1.5) * uu;
-    kn.M[i] = R(1) / (R(w_of(i)) * P);
+    kn.M[i] = rP * R(1.0 / w_of(i));
   }
   kn.ux = ux;
   kn.uy = uy;

@@ -56,10 +56,12 @@ __device__ __forceinline__ void node_tables2(Consts2<R>& k, R ux, R uy) {
   for (int i = 0; i < Q2; ++i) {
     const R cu = R(cx2(i)) * ux + R(cy2(i)) * uy;
     const R P = R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu;
+    // one reciprocal per population serves both quotients (correctly rounded in FP32)
+    const R rP = sizeof(R) == 4 ? R(__frcp_rn(float(P))) : R(1) / P;
     k.E[i] = R(w2(i)) * P;
-    k.K3[i] = R(3) * (R(1) / P - R(1));
+    k.K3[i] = R(3) * (rP - R(1));
     k.L[i] = log(P) - R(3) * cu + R(1.5) * uu;
-    k.M[i] = R(1) / (R(w2(i)) * P);
+    k.M[i] = rP * R(1.0 / w2(i));
   }
   k.ux = ux;
   k.uy = uy;

@@ -157,11 +157,18 @@ def _compare(name, gpu, ref, tol, excusable):
     assert worst_excused < max(1e-3, 50 * tol), (name, worst_excused)
 
 
-@pytest.mark.parametrize("prec", ["f32", "f16dev", "bf16dev"])
-def test_plume_256_sampled(E, prec):
+@pytest.mark.parametrize("prec,background", [("f32", 0.0), ("f16dev", 0.0), ("bf16dev", 0.0), ("f32", 0.1),
+                                             ("f16dev", 0.1)])
+def test_plume_256_sampled(E, prec, background):
+    """The bench's plume and launch.  With background > 0 a periodic mode
+    background (1 + 0.5 sin(2 pi (x + 2y + 3z) / 256)) is added, so the field varies across every
+    periodic seam (the plume alone leaves the faces at phi ~ e^-128, and a uniform background
+    would make both sides of a seam equal): a wrong wrap in x, y or z of the staged rows then
+    moves sampled boundary nodes by ~1e-3 of their size, far above the bound."""
     wl = synth.gaussian_plume(n=256)
     lat = gpu_lattice(E, wl.dims, prec, D=wl.D, u=wl.u, theta=3e-4)
-    E.elbm_init_equilibrium(lat.h, torch.as_tensor(wl.phi0, dtype=torch.float32, device="cuda"))
+    phi0 = wl.phi0 + (synth.sine_mode(wl.dims, (1, 2, 3), c0=background, amp=0.5 * background) if background else 0.0)
+    E.elbm_init_equilibrium(lat.h, torch.as_tensor(phi0, dtype=torch.float32, device="cuda"))
     E.elbm_step(lat.h, 40)
     g0 = torch.empty((27,) + wl.dims[::-1], dtype=torch.float32, device="cuda")
     E.elbm_read_populations(lat.h, g0)
@@ -177,7 +184,7 @@ def test_plume_256_sampled(E, prec):
                           (np.asarray(wl.meta["mu0"]) + np.random.default_rng(2).normal(0, 10, (1500, 3))).astype(int) % 256])
     S = O.relaxation_matrix(torch.as_tensor(wl.D))
     ref, exc = _oracle_one_step(g0, wl.dims, pts, torch.as_tensor(wl.u), lambda x, y, z: S, 3e-4)
-    _compare(f"plume256 {prec}", _gpu_at(g1, wl.dims, pts), ref, TOL[prec], exc)
+    _compare(f"plume256 {prec} background {background}", _gpu_at(g1, wl.dims, pts), ref, TOL[prec], exc)
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16dev"])
