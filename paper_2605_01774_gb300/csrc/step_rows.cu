@@ -48,27 +48,59 @@ __host__ __device__ constexpr size_t stage_bytes(int W) {
 
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
+// Layout of one stage: the 27 pulled population rows (and, for the deviation storages, the 9
+// scale rows), then optionally the destination row's 6 T-field rows and its source row, so that
+// the collision reads every per-node input from shared memory.  Offsets 0 = not staged.
+struct StageFmt {
+  unsigned bytes;     // bytes one row's copies deliver (the expect-tx count)
+  unsigned t_off;     // the T rows (6 W values of the arithmetic type), or 0
+  unsigned src_off;   // the source row (W floats), or 0
+};
+
+template <typename Elem>
+StageFmt stage_fmt(int W, bool has_T, bool has_src, size_t budget) {
+  using R = typename Storage<Elem>::real;
+  StageFmt f{(unsigned)stage_bytes<Elem>(W), 0u, 0u};
+  const size_t t = has_T ? 6ull * W * sizeof(R) : 0, r = has_src ? (size_t)W * sizeof(float) : 0;
+  if (t + r > 0 && STAGES * (f.bytes + t + r) <= budget) {
+    if (has_T) f.t_off = f.bytes;
+    if (has_src) f.src_off = f.bytes + (unsigned)t;
+    f.bytes += (unsigned)(t + r);
+  }
+  return f;
+}
+
 // Copies of one row of length W, spread over the lanes of warp 0 (lane 0 posts the byte
 // count first).
 template <typename Elem>
-__device__ void issue_row(const Field<Elem>& in, const Grid& G, int W, int row, unsigned char* stage, uint64_t* bar) {
+__device__ void issue_row(const Field<Elem>& in, const Grid& G, int W, int row, unsigned char* stage, uint64_t* bar,
+                          const StageFmt& sf, const typename Storage<Elem>::real* T6, const float* src) {
+  using R = typename Storage<Elem>::real;
   const int lane = threadIdx.x & 31;
   const int Ny = G.ny, Nz = G.nz;
   const int y = row % Ny, z = row / Ny;
-  if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)stage_bytes<Elem>(W));
+  if (lane == 0) mbar_arrive_expect_tx(bar, sf.bytes);
   __syncwarp();
   constexpr bool dev = Storage<Elem>::dev;
+  constexpr int nbase = dev ? 36 : 27;
   Elem* planes = reinterpret_cast<Elem*>(stage);
   float* srows = reinterpret_cast<float*>(stage + 27ull * W * sizeof(Elem));
-  for (int c = lane; c < (dev ? 36 : 27); c += 32) {
+  const int ncopies = nbase + (sf.t_off ? 6 : 0) + (sf.src_off ? 1 : 0);
+  for (int c = lane; c < ncopies; c += 32) {
     if (c < 27) {
       const int ys = wrap(y - cy_of(c), Ny), zs = wrap(z - cz_of(c), Nz);
       bulk_copy_g2s(planes + (size_t)c * W, in.pops + (size_t)c * G.N + (size_t)(ys + Ny * zs) * W,
                     W * sizeof(Elem), bar);
-    } else if constexpr (dev) {
+    } else if (dev && c < nbase) {
       const int r = c - 27;                              // scale row r = 3 (cy + 1) + (cz + 1)
       const int ys = wrap(y - (r / 3 - 1), Ny), zs = wrap(z - (r % 3 - 1), Nz);
       bulk_copy_g2s(srows + (size_t)r * W, in.scale + (size_t)(ys + Ny * zs) * W, W * sizeof(float), bar);
+    } else if (sf.t_off && c < nbase + 6) {
+      const int q = c - nbase;                           // T component q of the destination row
+      bulk_copy_g2s(stage + sf.t_off + (size_t)q * W * sizeof(R), T6 + (size_t)q * G.N + (size_t)row * W,
+                    W * sizeof(R), bar);
+    } else {
+      bulk_copy_g2s(stage + sf.src_off, src + (size_t)row * W, W * sizeof(float), bar);
     }
   }
 }
@@ -147,14 +179,14 @@ __global__ void __launch_bounds__(block_threads(WC), rows_min_blocks<Elem, WC>()
 k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G,
             const typename Storage<Elem>::real* __restrict__ T6, const float* __restrict__ src,
             const float* __restrict__ u3, int fallback, unsigned long long* __restrict__ counters,
-            long long wait_limit, const PopConsts<typename Storage<Elem>::real> k) {
+            long long wait_limit, StageFmt sf, const PopConsts<typename Storage<Elem>::real> k) {
   using R = typename Storage<Elem>::real;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[STAGES];
   __shared__ int s_row[STAGES];
   __shared__ int abort_flag;
   const int W = WC > 0 ? WC : G.nx;
-  const size_t SB = stage_bytes<Elem>(W);
+  const size_t SB = sf.bytes;
   const int nrows = G.ny * G.nz;
   const bool producer = threadIdx.x < 32;     // warp 0 takes the rows and issues their copies
   if (threadIdx.x == 0) {
@@ -172,7 +204,7 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
     for (int m = 0; m < STAGES - 1; ++m) {
       const int row = take_row(counters, nrows, exhausted);
       if (threadIdx.x == 0) s_row[m] = row;
-      if (row < nrows) issue_row(in, G, W, row, smem + m * SB, &bars[m]);
+      if (row < nrows) issue_row(in, G, W, row, smem + m * SB, &bars[m], sf, T6, src);
     }
     if (!exhausted && threadIdx.x == 0) pend = atomicAdd(counters + TICKET, 1ull);
   }
@@ -199,7 +231,7 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
       }
       if (threadIdx.x == 0) s_row[sm] = nrow;
       // ordering of the previous reads of this buffer before the copies: the block barrier
-      if (nrow < nrows) issue_row(in, G, W, nrow, smem + sm * SB, &bars[sm]);
+      if (nrow < nrows) issue_row(in, G, W, nrow, smem + sm * SB, &bars[sm], sf, T6, src);
     }
     if (!mbar_wait_bounded(&bars[s], (it / STAGES) & 1, wait_limit)) {
       abort_flag = 1;
@@ -213,11 +245,18 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
         if (G.dirichlet) abb_faces<Elem, R>(g, in, G, x, n, k);
         if (src != nullptr) {
           // merged Strang half-steps of consecutive steps (Section 3.3)
-          const R r = k.src_step * R(__ldg(src + n));
+          const float sv = sf.src_off ? reinterpret_cast<const float*>(stage + sf.src_off)[x] : __ldg(src + n);
+          const R r = k.src_step * R(sv);
 #pragma unroll
           for (int i = 0; i < Q; ++i) g[i] += r * k.E[i];
         }
-        const Sym6<R> T = load_T<R>(T6, G.N, n, k.T);
+        Sym6<R> T;
+        if (sf.t_off) {
+          const R* Ts = reinterpret_cast<const R*>(stage + sf.t_off);
+          T = Sym6<R>{Ts[x], Ts[W + x], Ts[2 * W + x], Ts[3 * W + x], Ts[4 * W + x], Ts[5 * W + x]};
+        } else {
+          T = load_T<R>(T6, G.N, n, k.T);
+        }
         R phi;
         bool t;
         if constexpr (VEL == 2) {
@@ -383,7 +422,7 @@ k_step_pipe(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
       }
       if (lane == 0) s_row[s] = row;             // released by the arrival on full[s]
       if (row < nrows) {
-        issue_row(in, G, W, row, smem + s * SB, &full[s]);
+        issue_row(in, G, W, row, smem + s * SB, &full[s], StageFmt{(unsigned)SB, 0u, 0u}, T6, src);
         k_real = kk + 1;
       } else {
         if (lane == 0) mbar_arrive(&full[s]);
@@ -465,24 +504,26 @@ k_step_pipe(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
 
 namespace {
 
-// Blocks of k_step_rows<Elem, VEL, ROOT, WC> resident per SM at row length W (0: not
-// launchable); raises the kernel's dynamic shared-memory limit as needed.  Cached per
-// (device, W).
+// Blocks of k_step_rows<Elem, VEL, ROOT, WC> resident per SM with `dyn` bytes of stages (0: not
+// launchable); raises the kernel's dynamic shared-memory limit as needed.  Cached per (device, dyn).
 template <typename Elem, int VEL, bool ROOT, int WC>
-int rows_occupancy(int W) {
-  static int c_dev = -1, c_w = -1, c_nb = 0;
+int rows_occupancy(size_t dyn) {
+  static int c_dev[4] = {-1, -1, -1, -1}, c_nb[4] = {0, 0, 0, 0};
+  static size_t c_dyn[4] = {0, 0, 0, 0};
+  static int next = 0;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (dev == c_dev && W == c_w) return c_nb;
-  const size_t dyn = STAGES * stage_bytes<Elem>(W);
+  for (int e = 0; e < 4; ++e)
+    if (c_dev[e] == dev && c_dyn[e] == dyn) return c_nb[e];
   int nb = 0;
   if (cudaFuncSetAttribute(k_step_rows<Elem, VEL, ROOT, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) ==
           cudaSuccess &&
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<Elem, VEL, ROOT, WC>, block_threads(WC), dyn) ==
           cudaSuccess) {
-    c_dev = dev;
-    c_w = W;
-    c_nb = nb;
+    c_dev[next] = dev;
+    c_dyn[next] = dyn;
+    c_nb[next] = nb;
+    next = (next + 1) % 4;
     return nb;
   }
   cudaGetLastError();
@@ -492,8 +533,20 @@ int rows_occupancy(int W) {
 template <typename Elem, int VEL, bool ROOT, int WC>
 cudaError_t launch_rows_t(const StepLaunch& L, cudaStream_t s) {
   using R = typename Storage<Elem>::real;
-  const int nb = rows_occupancy<Elem, VEL, ROOT, WC>(L.nx);
+  // stage the T-field and source rows too where that keeps the resident blocks per SM
+  const StageFmt base = stage_fmt<Elem>(L.nx, false, false, 0);
+  StageFmt sf = stage_fmt<Elem>(L.nx, L.T6 != nullptr, L.src != nullptr, 200 * 1024);
+  int nb = rows_occupancy<Elem, VEL, ROOT, WC>(STAGES * (size_t)base.bytes);
+  if (sf.bytes != base.bytes) {
+    const int nbf = rows_occupancy<Elem, VEL, ROOT, WC>(STAGES * (size_t)sf.bytes);
+    if (nbf >= nb && nbf > 0) nb = nbf;
+    else sf = base;
+  }
   if (nb <= 0) return cudaErrorNotSupported;
+  // the launch below raises the kernel's shared-memory limit to this launch's stages
+  if (cudaFuncSetAttribute(k_step_rows<Elem, VEL, ROOT, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(STAGES * (size_t)sf.bytes)) != cudaSuccess)
+    return cudaGetLastError();
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -503,9 +556,9 @@ cudaError_t launch_rows_t(const StepLaunch& L, cudaStream_t s) {
   Grid G{L.nx, L.ny, L.nz, L.N, L.dirichlet};
   const PopConsts<R>& k = *reinterpret_cast<const PopConsts<R>*>(std::is_same<R, double>::value ? (const void*)L.kd
                                                                                                : (const void*)L.kf);
-  k_step_rows<Elem, VEL, ROOT, WC><<<grid, block_threads(WC), STAGES * stage_bytes<Elem>(L.nx), s>>>(
+  k_step_rows<Elem, VEL, ROOT, WC><<<grid, block_threads(WC), STAGES * (size_t)sf.bytes, s>>>(
       in, static_cast<Elem*>(L.pout), L.sout, G, static_cast<const R*>(L.T6), L.src, L.u3, L.fallback, L.counters,
-      L.wait_limit > 0 ? L.wait_limit : WAIT_LIMIT, k);
+      L.wait_limit > 0 ? L.wait_limit : WAIT_LIMIT, sf, k);
   return cudaGetLastError();
 }
 
