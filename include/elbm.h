@@ -133,13 +133,19 @@ elbm_status elbm_set_lambda_mode(elbm_handle h, int32_t mode);
  *     faster there on the 256^3 plume and the 384^3 heterogeneous workload), else 1.
  *   1 one thread per node gathering its 27 pulled populations from global memory.
  *   2 persistent blocks taking x-rows from a ticket counter and staging each row's 27
- *     pulled source rows (and, for the deviation storages, the 9 scale rows) in shared
+ *     pulled source rows (and, for the deviation storages, the 9 scale rows; with a tensor
+ *     field or a source also the row's 6 T rows and source row where they fit) in shared
  *     memory with asynchronous bulk copies, two buffers deep; needs nx % 8 == 0 and the
  *     buffers within 200 KiB: nx <= 472 in FP64, 944 in FP32, 1136 in the deviation
  *     storages.
- * ELBM_ERR_ARG for other values, ELBM_ERR_UNSUPPORTED for 2 where it is not available.
+ *   3 no block barrier per row: persistent blocks (two per SM, one for FP64), each a producer
+ *     warp feeding a ring of row stages (per-stage full/empty mbarriers) to consumer warps that
+ *     take 32-node segments and release a stage once their populations are loaded; needs
+ *     nx % 8 == 0 and at least three stages in shared memory.  Measured no faster than 2 on
+ *     GB300 (the default never picks it).
+ * ELBM_ERR_ARG for other values, ELBM_ERR_UNSUPPORTED for 2 or 3 where it is not available.
  * A bounded staging wait that gives up makes the next elbm_synchronize or elbm_reduce
- * return ELBM_ERR_TIMEOUT. */
+ * return ELBM_ERR_TIMEOUT (see elbm_set_wait_limit). */
 elbm_status elbm_set_step_kernel(elbm_handle h, int32_t variant);
 
 /* Limit, in SM clock cycles, of every wait of the staged-row step kernels (variants 2 and 3)

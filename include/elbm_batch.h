@@ -70,7 +70,7 @@ elbm_status elbm_batch_step(elbm_batch_handle h, int64_t nsteps, int32_t mode);
 elbm_status elbm_batch_synchronize(elbm_batch_handle h);
 
 /* Time `steps_per_trial` mode-0 steps for each candidate block shape (threads per
- * block 64, 128 or 256, resident blocks per SM 1 .. occupancy) and keep the fastest.
+ * block 128 or 256, resident blocks per SM 1 .. occupancy) and keep the fastest.
  * The trials advance the state: re-initialise afterwards. */
 elbm_status elbm_batch_autotune(elbm_batch_handle h, int32_t steps_per_trial, int32_t* tile_out,
                                 int32_t* blocks_per_sm_out);

@@ -568,13 +568,13 @@ elbm_status elbm_batch_autotune(elbm_batch_handle h, int32_t steps_per_trial, in
                                 int32_t* blocks_per_sm_out) {
   if (!h || steps_per_trial < 1) return bfail(h, ELBM_ERR_ARG, "bad argument");
   if (!h->initialized) return bfail(h, ELBM_ERR_STATE, "not initialised");
-  // candidates: threads per block (tile) 64, 128 or 256; resident blocks per SM 1..occupancy
+  // candidates: threads per block (tile) 128 or 256; resident blocks per SM 1..occupancy
   int best_b = h->blocks_per_sm, best_t = h->tile;
   float best_ms = 1e30f;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int t : {64, 128, 256})
+  for (int t : {128, 256})
   for (int b = 1;; ++b) {
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_persistent, t, 0);

@@ -516,8 +516,12 @@ int rows_occupancy(size_t dyn) {
   for (int e = 0; e < 4; ++e)
     if (c_dev[e] == dev && c_dyn[e] == dyn) return c_nb[e];
   int nb = 0;
-  if (cudaFuncSetAttribute(k_step_rows<Elem, VEL, ROOT, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) ==
-          cudaSuccess &&
+  // raise (never lower) the kernel's limit: another layout may already have been launched
+  cudaFuncAttributes fa;
+  const int cur = cudaFuncGetAttributes(&fa, k_step_rows<Elem, VEL, ROOT, WC>) == cudaSuccess
+                      ? fa.maxDynamicSharedSizeBytes : 0;
+  if ((cur >= (int)dyn || cudaFuncSetAttribute(k_step_rows<Elem, VEL, ROOT, WC>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) == cudaSuccess) &&
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_rows<Elem, VEL, ROOT, WC>, block_threads(WC), dyn) ==
           cudaSuccess) {
     c_dev[next] = dev;
@@ -543,12 +547,20 @@ cudaError_t launch_rows_t(const StepLaunch& L, cudaStream_t s) {
     else sf = base;
   }
   if (nb <= 0) return cudaErrorNotSupported;
-  // the launch below raises the kernel's shared-memory limit to this launch's stages
-  if (cudaFuncSetAttribute(k_step_rows<Elem, VEL, ROOT, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(STAGES * (size_t)sf.bytes)) != cudaSuccess)
-    return cudaGetLastError();
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
+  // the kernel's shared-memory limit only ever grows (rows_occupancy raised it for both layouts);
+  // raise it here only if this launch needs more, so that steps do not change a kernel attribute
+  static int c_dev = -1;
+  static size_t c_max = 0;
+  const size_t dyn = STAGES * (size_t)sf.bytes;
+  if (dev != c_dev || dyn > c_max) {
+    if (cudaFuncSetAttribute(k_step_rows<Elem, VEL, ROOT, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)std::max(dyn, dev == c_dev ? c_max : (size_t)0)) != cudaSuccess)
+      return cudaGetLastError();
+    c_max = std::max(dyn, dev == c_dev ? c_max : (size_t)0);
+    c_dev = dev;
+  }
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const long long nrows = (long long)L.ny * L.nz;
   const int grid = (int)std::min<long long>(nrows, (long long)nb * nsm);

@@ -1,7 +1,7 @@
 """The implementations of the fused collide-stream step (Eq. method-lbe with the collision of
 Section 2): one thread per node gathering from global memory (variant 1), persistent blocks
 staging the pulled x-rows in shared memory with bulk asynchronous copies and a block barrier
-per row (variant 2), and one block per SM with a producer warp feeding a ring of row stages
+per row (variant 2), and persistent blocks each with a producer warp feeding a ring of row stages
 through full/empty mbarriers to consumer warps that take 32-node segments (variant 3).  They
 evaluate the same arithmetic in the same order, so their outputs must be bit-equal; the staged
 kernels are also checked against the FP64 oracle on their own."""
