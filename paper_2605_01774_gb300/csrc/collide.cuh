@@ -234,9 +234,11 @@ __device__ __forceinline__ bool collide_node(R (&g)[Q], const Sym6<R>& T, const 
       }
     }
     if (!scanned) {
+      // min by fmin (one min instruction per population; a NaN population is skipped, and a
+      // NaN node stays NaN whichever way the test goes)
       R mn = gs[0];
 #pragma unroll
-      for (int i = 1; i < Q; ++i) mn = mn < gs[i] ? mn : gs[i];
+      for (int i = 1; i < Q; ++i) mn = fmin(mn, gs[i]);
       any = mn < k.eps;
     }
     if (any) {
@@ -252,10 +254,10 @@ __device__ __forceinline__ bool collide_node(R (&g)[Q], const Sym6<R>& T, const 
           // shortened populations by the same order as the FP32 update itself.
           const R r = sizeof(R) == 4 ? R(__fdividef(float(g[i] - k.eps), float(g[i] - gs[i])))
                                      : (g[i] - k.eps) / (g[i] - gs[i]);
-          alpha = r < alpha ? r : alpha;
+          alpha = fmin(r, alpha);
         }
       }
-      alpha = alpha > R(0) ? alpha : R(0);
+      alpha = fmax(alpha, R(0));
 #pragma unroll
       for (int i = 0; i < Q; ++i) gs[i] = g[i] + alpha * (gs[i] - g[i]);
     }

@@ -20,9 +20,14 @@
 #ifndef ELBM_ROWS_STAGES
 #define ELBM_ROWS_STAGES 2
 #endif
-// Resident 256-thread blocks per SM requested from the register allocator.
+// Resident 256-thread blocks per SM requested from the register allocator: FP32 storage (80
+// registers), deviation storages (64 registers; measured on the 256^3 plume, 0.726 -> 0.701
+// ms/step over 600 steps for FP16 with four blocks instead of three).
 #ifndef ELBM_ROWS_MINB
 #define ELBM_ROWS_MINB 3
+#endif
+#ifndef ELBM_ROWS_MINB_DEV
+#define ELBM_ROWS_MINB_DEV 4
 #endif
 
 namespace elbm {
@@ -107,8 +112,11 @@ __device__ void issue_row(const Field<Elem>& in, const Grid& G, int W, int row, 
 
 // Populations of node x from the staged row: plane i holds source row (y - c_iy, z - c_iz),
 // of which node x pulls element x - c_ix (periodic wrap: xm = x - 1, xp = x + 1 mod W).
+// Es: the equilibrium shape E_i of the deviation storages, a shared-memory copy of the block
+// (read afresh in every row: held in registers across the row loop, the 27 values make the
+// kernel spill).
 template <typename Elem, typename R>
-__device__ __forceinline__ void staged_pull(R (&g)[Q], const unsigned char* stage, int W, int x, const PopConsts<R>& k) {
+__device__ __forceinline__ void staged_pull(R (&g)[Q], const unsigned char* stage, int W, int x, const float* Es) {
   const int xm = x == 0 ? W - 1 : x - 1, xp = x == W - 1 ? 0 : x + 1;
   const Elem* P = reinterpret_cast<const Elem*>(stage);
   if constexpr (Storage<Elem>::dev) {
@@ -117,7 +125,7 @@ __device__ __forceinline__ void staged_pull(R (&g)[Q], const unsigned char* stag
     for (int i = 0; i < Q; ++i) {
       const int xs = cx_of(i) == 1 ? xm : (cx_of(i) == -1 ? xp : x);
       const float s = S[(i % 9) * W + xs];
-      g[i] = s * Codec<Elem>::fma_pow2(P[i * W + xs], qexp_of(i), k.E[i]);
+      g[i] = s * Codec<Elem>::fma_pow2(P[i * W + xs], qexp_of(i), Es[i]);
     }
   } else {
 #pragma unroll
@@ -147,10 +155,14 @@ __device__ __forceinline__ void abb_faces(R (&g)[Q], const Field<Elem>& f, const
 }
 
 // Resident blocks per SM requested from the register allocator: 768 threads for FP32 storage
-// types (3 x 256 or 2 x 384), one block for FP64.
+// types (3 x 256 or 2 x 384), 4 x 256 for the deviation storages at the compiled-in row length
+// 256 or 512 (the velocity-field and exact-root kernels keep 3: their per-node tables need the
+// registers), one block for FP64.
 template <typename Elem, int WC>
 constexpr int rows_min_blocks() {
-  return std::is_same<Elem, double>::value ? 1 : (block_threads(WC) == 384 ? 2 : ELBM_ROWS_MINB);
+  return std::is_same<Elem, double>::value
+             ? 1
+             : (block_threads(WC) == 384 ? 2 : (Storage<Elem>::dev && WC > 0 ? ELBM_ROWS_MINB_DEV : ELBM_ROWS_MINB));
 }
 
 }  // namespace
@@ -185,6 +197,8 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
   __shared__ uint64_t bars[STAGES];
   __shared__ int s_row[STAGES];
   __shared__ int abort_flag;
+  __shared__ float sE[Q];                     // E_i for the deviation decode (ordered by the first barrier)
+  if (threadIdx.x < Q) sE[threadIdx.x] = float(k.E[threadIdx.x]);
   const int W = WC > 0 ? WC : G.nx;
   const size_t SB = sf.bytes;
   const int nrows = G.ny * G.nz;
@@ -241,7 +255,7 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
       for (int x = threadIdx.x; x < W; x += block_threads(WC)) {
         const int n = (int)(row0 + x);
         R g[Q];
-        staged_pull<Elem, R>(g, stage, W, x, k);
+        staged_pull<Elem, R>(g, stage, W, x, sE);
         if (G.dirichlet) abb_faces<Elem, R>(g, in, G, x, n, k);
         if (src != nullptr) {
           // merged Strang half-steps of consecutive steps (Section 3.3)
@@ -371,6 +385,8 @@ k_step_pipe(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
   __shared__ int s_row[PIPE_MAX_STAGES];
   __shared__ int s_item;
   __shared__ int abort_flag;
+  __shared__ float sE[Q];                     // E_i for the deviation decode (ordered by the first barrier)
+  if (threadIdx.x < Q) sE[threadIdx.x] = float(k.E[threadIdx.x]);
   const int W = WC > 0 ? WC : G.nx;
   const int nseg = (W + 31) >> 5;
   const size_t SB = stage_bytes<Elem>(W);
@@ -465,7 +481,7 @@ k_step_pipe(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
     if (row >= nrows) break;
     const int x = (q << 5) + lane;
     R g[Q];
-    if (x < W) staged_pull<Elem, R>(g, smem + s * SB, W, x, k);
+    if (x < W) staged_pull<Elem, R>(g, smem + s * SB, W, x, sE);
     // the lane's populations are in registers: release the stage before the collision, so a
     // slow segment holds its stage only for its loads (the arrival orders them before any
     // later copy into the stage)
