@@ -43,7 +43,8 @@ F64_FLOPS_PER_NODE = 706   # mean of the two launches in profiles/k_step_fp64_pl
 BYTES_PER_NODE = {"f64": 27 * 8 * 2, "f32": 27 * 4 * 2, "f16dev": (27 * 2 + 4) * 2, "bf16dev": (27 * 2 + 4) * 2}
 WORKLOAD = ("advected anisotropic Gaussian plume 256^3 periodic, u=(0.05,0.03,0.02), "
             "D=R diag(0.1,1e-3,1e-5) R^T (seeded ZYZ, seed 2), sigma0=8")
-KERNEL_SOURCES = ["collide.cuh", "storage.cuh", "pull.cuh", "step.cu", "step_rows.cu", "bulk.cuh", "lattice.cuh"]
+KERNEL_SOURCES = ["collide.cuh", "eqlog.cuh", "storage.cuh", "pull.cuh", "step.cu", "step_rows.cu", "bulk.cuh",
+                  "lattice.cuh"]
 THETA = 3e-4   # stabilizer guard used by every form, so the forms differ only in arithmetic and storage
 
 

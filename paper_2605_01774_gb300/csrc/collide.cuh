@@ -15,6 +15,7 @@
 // above 1e-30 (FP32) / 1e-300 (FP64), below which the H-products are not resolvable.
 // The positivity fallback (Eq. method-alpha) shortens g* - g when some g*_i < eps.
 #pragma once
+#include "eqlog.cuh"
 #include "lattice.cuh"
 
 namespace elbm {
@@ -126,13 +127,17 @@ __device__ __forceinline__ void node_tables(PopConsts<R>& kn, R ux, R uy, R uz) 
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const R cu = R(cx_of(i)) * ux + R(cy_of(i)) * uy + R(cz_of(i)) * uz;
-    const R P = R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu;
-    // one reciprocal per population serves both quotients (correctly rounded in FP32)
-    const R rP = sizeof(R) == 4 ? R(__frcp_rn(float(P))) : R(1) / P;
-    kn.E[i] = R(w_of(i)) * P;
-    kn.K3[i] = R(3) * (rP - R(1));
-    kn.L[i] = log(P) - R(3) * cu + R(1.5) * uu;
-    kn.M[i] = rP * R(1.0 / w_of(i));
+    if constexpr (sizeof(R) == 4) {
+      eq_tables_f32(fmaf(3.0f, cu, __fmul_rn(-1.5f, uu)), __fmul_rn(__fmul_rn(4.5f, cu), cu), float(w_of(i)), kn.E[i],
+                    kn.K3[i], kn.L[i], kn.M[i]);
+    } else {
+      const R P = R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu;
+      const R rP = R(1) / P;   // one quotient serves K3 and M
+      kn.E[i] = R(w_of(i)) * P;
+      kn.K3[i] = R(3) * (rP - R(1));
+      kn.L[i] = log(P) - R(3) * cu + R(1.5) * uu;
+      kn.M[i] = rP * R(1.0 / w_of(i));
+    }
   }
   kn.ux = ux;
   kn.uy = uy;

@@ -21,6 +21,7 @@
 #include <type_traits>
 
 #include "../../include/elbm2d.h"
+#include "eqlog.cuh"
 
 namespace {
 
@@ -55,13 +56,17 @@ __device__ __forceinline__ void node_tables2(Consts2<R>& k, R ux, R uy) {
 #pragma unroll
   for (int i = 0; i < Q2; ++i) {
     const R cu = R(cx2(i)) * ux + R(cy2(i)) * uy;
-    const R P = R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu;
-    // one reciprocal per population serves both quotients (correctly rounded in FP32)
-    const R rP = sizeof(R) == 4 ? R(__frcp_rn(float(P))) : R(1) / P;
-    k.E[i] = R(w2(i)) * P;
-    k.K3[i] = R(3) * (rP - R(1));
-    k.L[i] = log(P) - R(3) * cu + R(1.5) * uu;
-    k.M[i] = rP * R(1.0 / w2(i));
+    if constexpr (sizeof(R) == 4) {
+      elbm::eq_tables_f32(fmaf(3.0f, cu, __fmul_rn(-1.5f, uu)), __fmul_rn(__fmul_rn(4.5f, cu), cu), float(w2(i)),
+                          k.E[i], k.K3[i], k.L[i], k.M[i]);
+    } else {
+      const R P = R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu;
+      const R rP = R(1) / P;   // one quotient serves K3 and M
+      k.E[i] = R(w2(i)) * P;
+      k.K3[i] = R(3) * (rP - R(1));
+      k.L[i] = log(P) - R(3) * cu + R(1.5) * uu;
+      k.M[i] = rP * R(1.0 / w2(i));
+    }
   }
   k.ux = ux;
   k.uy = uy;

@@ -139,6 +139,34 @@ def test_fp32_against_fp64_oracle(E, dims):
     lat.close()
 
 
+def test_fp32_large_velocity_tables(E):
+    """Per-node velocities up to |u| = 0.2: the FP32 tables of a node's own u switch from the
+    artanh series to logf where |s| = |t / (2 + t)| > 0.3 (|c.u| about 0.24 and above), so both
+    branches are taken in one lattice; phi after 20 steps against the FP64 oracle with the same
+    fields, to the FP32 bound of the other D2Q9 tests."""
+    nx, ny = 64, 48
+    uf, D3, phi0 = _fields(nx, ny, 5)
+    x = np.arange(nx)[None, :] * np.ones((ny, 1))
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    amp = 0.1 + 0.1 * np.sin(2 * np.pi * x / nx) * np.cos(2 * np.pi * y / ny)      # 0 .. 0.2
+    uf = np.stack([amp * np.cos(0.6), amp * np.sin(0.6)])
+    cu = np.abs(uf[0]) + np.abs(uf[1])
+    t = 3 * cu + 4.5 * cu ** 2 - 1.5 * (uf ** 2).sum(0)
+    assert (np.abs(t / (2 + t)) > 0.3).mean() > 0.05 and (np.abs(t / (2 + t)) <= 0.3).mean() > 0.5
+    lat = _lattice(E, (nx, ny), "f32", ufield=uf, D3=D3)
+    E.elbm2d_init_equilibrium(lat.h, torch.as_tensor(phi0, dtype=torch.float32, device="cuda"))
+    E.elbm2d_step(lat.h, 20)
+    phi = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
+    E.elbm2d_read_moments(lat.h, phi)
+    torch.cuda.synchronize()
+    uf32 = torch.as_tensor(uf.astype(np.float32).astype(np.float64))
+    prob = O2.Problem(u=uf32, S=_S_field(D3.astype(np.float32).astype(np.float64)), theta=3e-4)
+    ref = O2.run(O2.init_equilibrium(phi0.astype(np.float32).astype(np.float64), uf32), prob, 20).sum(0)
+    err = float(torch.linalg.vector_norm(phi.cpu() - ref) / torch.linalg.vector_norm(ref))
+    assert err < 2e-6, err
+    lat.close()
+
+
 def test_arguments(E):
     L = E.lib()
     import ctypes as C
