@@ -90,8 +90,14 @@ __device__ __forceinline__ void do_tile(const BatchArgs& a, const float* in, flo
   count_fallback(a, took);
 }
 
+// Resident 256-thread blocks per SM requested from the register allocator (0: no request; 4
+// forces 64 registers and spills, measured slower on the 512-domain sweep).
+#ifndef ELBM_BATCH_MINB
+#define ELBM_BATCH_MINB 0
+#endif
+
 // mode 1: one block per tile
-__global__ void __launch_bounds__(256) k_batch_step(BatchArgs a, int parity) {
+__global__ void __launch_bounds__(256, ELBM_BATCH_MINB) k_batch_step(BatchArgs a, int parity) {
   const float* in = parity ? a.bufB : a.bufA;
   float* out = parity ? a.bufA : a.bufB;
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) do_tile(a, in, out, t);
@@ -129,7 +135,7 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned expected, 
 }
 
 // mode 0: persistent kernel, all steps in one launch
-__global__ void __launch_bounds__(256) k_batch_persistent(BatchArgs a, int nsteps, int parity0, unsigned* bar,
+__global__ void __launch_bounds__(256, ELBM_BATCH_MINB) k_batch_persistent(BatchArgs a, int nsteps, int parity0, unsigned* bar,
                                                           unsigned expected, long long limit, int* err) {
   int parity = parity0;
   for (int s = 0; s < nsteps; ++s) {
