@@ -464,16 +464,19 @@ def elbm_adjoint_step(h, theta6, g, gbar_next=None, g_next=None, gbar=None, grad
 
 def tensor_misfit_function():
     """torch.autograd.Function whose forward is J(theta) and whose backward is the
-    hand-written adjoint (both computed by one elbm_adjoint_misfit call)."""
+    hand-written adjoint.  Where theta needs a gradient, one elbm_adjoint_misfit call runs the
+    forward sweep and the checkpointed reverse sweep and backward only scales the stored
+    gradient; otherwise (no_grad, or theta without requires_grad) only the forward sweep runs."""
     import torch
 
     class TensorMisfit(torch.autograd.Function):
         @staticmethod
         def forward(ctx, theta, handle, phi0, nsteps, obs_steps, targets):
-            grad = torch.empty_like(theta)
+            grad = torch.empty_like(theta) if ctx.needs_input_grad[0] else None
             J, nfb = elbm_adjoint_misfit(handle, theta.detach().contiguous(), phi0, nsteps, obs_steps, targets,
                                          grad6=grad)
-            ctx.save_for_backward(grad)
+            if grad is not None:
+                ctx.save_for_backward(grad)
             ctx.n_fallback = nfb
             return torch.tensor(J, dtype=torch.float64, device=theta.device)
 

@@ -103,6 +103,13 @@ def test_misfit_gradient_matches_fp64_cpu_adjoint(E):
     Jt = F.apply(th, h, torch.as_tensor(p["phi0"], device=DEV), 30, [15, 30], tg)
     Jt.backward()
     assert torch.allclose(th.grad, grad, rtol=1e-14, atol=0)
+    # without a gradient to compute (no_grad, or theta not requiring one) only the forward sweep
+    # runs; J is the same and the result carries no graph
+    with torch.no_grad():
+        Jn = F.apply(th, h, torch.as_tensor(p["phi0"], device=DEV), 30, [15, 30], tg)
+    Jd = F.apply(th.detach(), h, torch.as_tensor(p["phi0"], device=DEV), 30, [15, 30], tg)
+    assert Jn.item() == Jt.item() and Jd.item() == Jt.item()
+    assert not Jn.requires_grad and not Jd.requires_grad
     E.elbm_adjoint_destroy(h)
 
 
