@@ -128,9 +128,10 @@ elbm_status elbm_set_lambda_mode(elbm_handle h, int32_t mode);
 /* Which implementation of the fused collide-stream step (Eq. method-lbe with the collision
  * of Eqs. method-split..method-fallback) elbm_step launches; all give the same result up to
  * the order of floating-point operations, which is identical (bit-equal outputs).
- *   0 (default) auto: 2 for the FP32-arithmetic storages where nx is 256, 384 or 512 with
- *     a uniform velocity and the closed-form stabilizer (row length compiled in; measured
- *     faster there on the 256^3 plume and the 384^3 heterogeneous workload), else 1.
+ *   0 (default) auto: 2 for the FP32-arithmetic storages where nx >= 256 (row lengths 256,
+ *     384 and 512 compiled in) with a uniform velocity and the closed-form stabilizer
+ *     (measured faster there), else 1 (rows shorter than a block, per-node velocity fields,
+ *     the exact-root stabilizer and FP64 measured faster with 1).
  *   1 one thread per node gathering its 27 pulled populations from global memory.
  *   2 persistent blocks taking x-rows from a ticket counter and staging each row's 27
  *     pulled source rows (and, for the deviation storages, the 9 scale rows; with a tensor

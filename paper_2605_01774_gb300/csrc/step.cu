@@ -85,14 +85,16 @@ static cudaError_t launch_v(const StepLaunch& L, cudaStream_t s) {
 
 int step_variant(int prec, int nx, int vel, bool root, int requested) {
   if (requested != 0) return requested;
-  // auto: the staged-row kernel where its row length is compiled in (nx = 256, 384 or 512,
-  // uniform velocity, closed-form stabilizer) for the FP32-arithmetic storages, else the
-  // per-node kernel.  Measured, ms/step per-node -> staged: 256^3 plume FP32 0.684 -> 0.588,
-  // BF16 deviations 0.782 -> 0.769, FP16 deviations 0.777 -> 0.779; 384^3 heterogeneous
-  // (tensor field, source, Dirichlet) FP32 2.83 -> 2.48, FP16 2.88 -> 2.35, BF16 2.91 -> 2.36.
-  // FP64 (arithmetic-bound) keeps the per-node kernel.
-  if (prec != 0 && (nx == 256 || nx == 384 || nx == 512) && vel != 2 && !root && rows_eligible(prec, nx))
-    return 2;
+  // auto: the staged-row kernel for the FP32-arithmetic storages with rows of 256 nodes or more
+  // (uniform velocity, closed-form stabilizer), else the per-node kernel.  Measured, ms/step
+  // per-node -> staged: 256^3 plume FP32 0.684 -> 0.588, BF16 deviations 0.782 -> 0.769, FP16
+  // deviations 0.777 -> 0.779 (before the deviation kernels' spill fix); 384^3 heterogeneous
+  // (tensor field, source, Dirichlet) FP32 2.83 -> 2.48, FP16 2.88 -> 2.35; 320 x 256 x 256 (row
+  // length not compiled in) FP32 0.90 -> 0.72, FP16 1.00 -> 0.85.  Kept on the per-node kernel:
+  // rows shorter than a block (192^3: FP32 0.256 vs 0.279, FP16 0.279 vs 0.344), per-node
+  // velocity fields (256^3: FP32 1.23 vs 1.65, FP16 1.37 vs 1.77; the per-node tables need the
+  // registers the staged kernel's persistent loop holds) and FP64 (arithmetic-bound).
+  if (prec != 0 && nx >= 256 && vel != 2 && !root && rows_eligible(prec, nx)) return 2;
   return 1;
 }
 

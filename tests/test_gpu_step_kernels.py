@@ -165,6 +165,24 @@ def test_step_kernel_arguments(E):
     E.elbm_set_step_kernel(ok.h, 2)
 
 
+def test_automatic_choice(E):
+    """The automatic choice (measured on GB300): staged rows for the FP32-arithmetic storages
+    with rows of 256 nodes or more, compiled-in length or not; the per-node kernel for shorter
+    rows, per-node velocity fields, the exact-root stabilizer and FP64."""
+    cases = [((256, 2, 2), "f32", None, 2), ((320, 2, 2), "f16dev", None, 2), ((264, 2, 2), "bf16dev", None, 2),
+             ((192, 2, 2), "f32", None, 1), ((256, 2, 2), "f64", None, 1), ((256, 2, 2), "f32", "field", 1),
+             ((256, 2, 2), "f32", "root", 1)]
+    for dims, prec, mode, want in cases:
+        lat = E.Lattice(dims, prec)
+        if mode == "field":
+            E.elbm_set_velocity_field(lat.h, torch.full((3,) + dims[::-1], 0.01, device="cuda"))
+        elif mode == "root":
+            E.elbm_set_velocity_uniform(lat.h, (0.02, 0.01, 0.0))
+            E.elbm_set_lambda_mode(lat.h, 1)
+        assert E.elbm_get_step_kernel(lat.h) == want, (dims, prec, mode)
+        lat.close()
+
+
 @pytest.mark.parametrize("prec", ["f32", "f16dev"])
 @pytest.mark.parametrize("variant", [3])
 def test_staging_wait_limit_timeout_and_recovery(E, prec, variant):
