@@ -15,6 +15,8 @@
 // above 1e-30 (FP32) / 1e-300 (FP64), below which the H-products are not resolvable.
 // The positivity fallback (Eq. method-alpha) shortens g* - g when some g*_i < eps.
 #pragma once
+#include <type_traits>
+
 #include "eqlog.cuh"
 #include "lattice.cuh"
 
@@ -250,21 +252,30 @@ __device__ __forceinline__ bool collide_node(R (&g)[Q], const Sym6<R>& T, const 
       took = true;
       // alpha = min over Omega_i < 0 of (g_i - eps) / (-Omega_i), capped at 1.  A ratio is
       // below 1 exactly when g_i + Omega_i < eps, so only the violating populations need a
-      // quotient.
+      // quotient.  gs_i is replaced by d_i = -Omega_i = g_i - g*_i on the way, which the blend
+      // g_i + alpha (g*_i - g_i) = g_i - alpha d_i reuses; eps = 0 (the default) is its own
+      // loop, without the numerator's subtraction.
       R alpha = R(1);
+      auto scan = [&](auto eps0) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        if (gs[i] < k.eps && g[i] > gs[i]) {
-          // FP32: fast reciprocal-based quotient (2 ulp); the rounding of alpha moves the
-          // shortened populations by the same order as the FP32 update itself.
-          const R r = sizeof(R) == 4 ? R(__fdividef(float(g[i] - k.eps), float(g[i] - gs[i])))
-                                     : (g[i] - k.eps) / (g[i] - gs[i]);
-          alpha = fmin(r, alpha);
+        for (int i = 0; i < Q; ++i) {
+          const bool viol = gs[i] < k.eps && g[i] > gs[i];
+          const R d = g[i] - gs[i];
+          if (viol) {
+            const R n = decltype(eps0)::value ? g[i] : g[i] - k.eps;
+            // FP32: fast reciprocal-based quotient (2 ulp); the rounding of alpha moves the
+            // shortened populations by the same order as the FP32 update itself.
+            const R r = sizeof(R) == 4 ? R(__fdividef(float(n), float(d))) : n / d;
+            alpha = fmin(r, alpha);
+          }
+          gs[i] = d;
         }
-      }
+      };
+      if (k.eps == R(0)) scan(std::true_type{});
+      else scan(std::false_type{});
       alpha = fmax(alpha, R(0));
 #pragma unroll
-      for (int i = 0; i < Q; ++i) gs[i] = g[i] + alpha * (gs[i] - g[i]);
+      for (int i = 0; i < Q; ++i) gs[i] = fma(-alpha, gs[i], g[i]);
     }
   }
 #pragma unroll
