@@ -161,6 +161,17 @@ elbm_status elbm_set_step_kernel(elbm_handle h, int32_t variant);
  * ELBM_ERR_ARG if cycles < 0. */
 elbm_status elbm_set_wait_limit(elbm_handle h, int64_t cycles);
 
+/* Test hook for the bounded staging waits of variant 2 (no counterpart in the paper): with
+ * withheld = k > 0 every row-stage barrier of the staged-row kernel expects k more arrivals
+ * than the kernel makes, so the first staging wait of every block runs out after the limit of
+ * elbm_set_wait_limit.  The block then takes its abort path: the thread that issued the
+ * copies makes the k missing arrivals itself and waits (bounded) until the copies in flight
+ * have landed, and the next elbm_synchronize or elbm_reduce returns ELBM_ERR_TIMEOUT; the
+ * state is undefined until the next elbm_init_* or elbm_write_populations.  withheld = 0
+ * (the default) restores normal stepping.  Variants 1 and 3 ignore it.
+ * ELBM_ERR_ARG unless 0 <= withheld <= 8. */
+elbm_status elbm_set_wait_test(elbm_handle h, int32_t withheld);
+
 /* FP32 storage only (no effect on the others): with on = 1 (the default) each node update
  * puts the rounding of its 27 post-collision values back on its rest population c = 0, so the
  * stored node mass equals the conserved phi of Eq. (method-collision) up to one FP32

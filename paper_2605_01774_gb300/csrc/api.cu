@@ -39,6 +39,7 @@ struct elbm_ctx {
   int lambda_mode = 0;       // 0 closed form, 1 exact root
   int step_kernel = 0;       // 0 auto, 1 per-node gathers, 2 staged rows, 3 pipelined staged rows
   long long wait_limit = 0;  // staging-wait limit in clock cycles (0: the default, about one second)
+  int wait_withheld = 0;      // test hook: arrivals the staged-row barriers expect and never get
   int exact_mass = 1;        // FP32 storage: exact stored node mass
   std::string err;
 };
@@ -470,6 +471,7 @@ elbm_status elbm_step(elbm_handle h, int64_t nsteps) {
   L.kf = &h->kf;
   L.variant = h->step_kernel;
   L.wait_limit = h->wait_limit;
+  L.withheld = h->wait_withheld;
   for (int64_t s = 0; s < nsteps; ++s) {
     L.pin = h->pops[h->cur];
     L.sin = h->scale[h->cur];
@@ -506,6 +508,12 @@ elbm_status elbm_set_step_kernel(elbm_handle h, int32_t variant) {
 elbm_status elbm_set_wait_limit(elbm_handle h, int64_t cycles) {
   if (!h || cycles < 0) return fail(h, ELBM_ERR_ARG, "cycles must be >= 0");
   h->wait_limit = cycles;
+  return ELBM_OK;
+}
+
+elbm_status elbm_set_wait_test(elbm_handle h, int32_t withheld) {
+  if (!h || withheld < 0 || withheld > 8) return fail(h, ELBM_ERR_ARG, "withheld must be in [0, 8]");
+  h->wait_withheld = withheld;
   return ELBM_OK;
 }
 

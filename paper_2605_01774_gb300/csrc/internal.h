@@ -29,6 +29,7 @@ struct StepLaunch {
   int variant;                  // 0 auto, 1 one thread per node with global gathers, 2 staged rows,
                                 // 3 staged rows with a producer warp and per-stage full/empty barriers
   long long wait_limit;         // staging waits of variants 2 and 3 give up after this many cycles
+  int withheld;                 // variant 2, test hook: arrivals its stage barriers never get
 };
 cudaError_t launch_step(const StepLaunch& L, cudaStream_t s);
 // The implementation launch_step runs (1 per-node, 2 staged rows) for a requested variant

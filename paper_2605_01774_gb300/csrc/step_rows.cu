@@ -5,12 +5,15 @@
 // mbarrier, the 27 whole source rows the pull needs -- population plane i, row
 // (y - c_iy, z - c_iz) -- and, for the deviation storages, the 9 rows of the FP32 scale
 // plane.  The periodic x-shift is an index wrap inside the staged row.  STAGES buffers
-// rotate: the copies of the next STAGES - 1 rows are in flight while the current row is
-// collided, so memory parallelism does not depend on registers, and rows are handed out
-// dynamically so that blocks meeting costly rows (positivity fallback) do not set the
-// kernel's length.  Collision and store are those of the one-thread-per-node kernel,
-// in the same order, so both give bit-equal results.  Requires Nx % 8 == 0 (16-byte
-// aligned rows); every wait is bounded.
+// rotate without a block barrier: each warp counts itself on a stage once it has read its
+// nodes' populations into registers, and the last warp to do so refills that stage with the
+// next row (the row index is published with the stage's mbarrier), so the copies of the next
+// STAGES rows are in flight while the current one is collided, a warp that meets costly nodes
+// (positivity fallback, boundary faces) delays only the refill of the stage it is reading,
+// and memory parallelism does not depend on registers.  Rows are handed out dynamically so
+// that blocks meeting costly rows do not set the kernel's length.  Collision and store are
+// those of the one-thread-per-node kernel, in the same order, so both give bit-equal results.
+// Requires Nx % 8 == 0 (16-byte aligned rows); every wait is bounded.
 #include <algorithm>
 
 #include "bulk.cuh"
@@ -28,6 +31,18 @@
 #endif
 #ifndef ELBM_ROWS_MINB_DEV
 #define ELBM_ROWS_MINB_DEV 4
+#endif
+// 384-thread blocks (row length 384 compiled in) per SM requested from the register allocator
+// Shared memory (bytes, all stages) within which the destination row's T-field and source rows
+// are staged with the populations (0: read from global memory by each thread)
+#ifndef ELBM_ROWS_FIELD_BUDGET
+#define ELBM_ROWS_FIELD_BUDGET (200 * 1024)
+#endif
+#ifndef ELBM_ROWS_MINB_384
+#define ELBM_ROWS_MINB_384 2
+#endif
+#ifndef ELBM_ROWS_MINB_384_DEV
+#define ELBM_ROWS_MINB_384_DEV 2
 #endif
 
 namespace elbm {
@@ -75,23 +90,21 @@ StageFmt stage_fmt(int W, bool has_T, bool has_src, size_t budget) {
   return f;
 }
 
-// Copies of one row of length W, spread over the lanes of warp 0 (lane 0 posts the byte
-// count first).
+// Copies of one row of length W: those with index c = first, first + step, ... (the caller
+// posts the byte count on the mbarrier, sf.bytes, once per row).
 template <typename Elem>
-__device__ void issue_row(const Field<Elem>& in, const Grid& G, int W, int row, unsigned char* stage, uint64_t* bar,
-                          const StageFmt& sf, const typename Storage<Elem>::real* T6, const float* src) {
+__device__ void issue_copies(const Field<Elem>& in, const Grid& G, int W, int row, unsigned char* stage, uint64_t* bar,
+                             const StageFmt& sf, const typename Storage<Elem>::real* T6, const float* src, int first,
+                             int step) {
   using R = typename Storage<Elem>::real;
-  const int lane = threadIdx.x & 31;
   const int Ny = G.ny, Nz = G.nz;
   const int y = row % Ny, z = row / Ny;
-  if (lane == 0) mbar_arrive_expect_tx(bar, sf.bytes);
-  __syncwarp();
   constexpr bool dev = Storage<Elem>::dev;
   constexpr int nbase = dev ? 36 : 27;
   Elem* planes = reinterpret_cast<Elem*>(stage);
   float* srows = reinterpret_cast<float*>(stage + 27ull * W * sizeof(Elem));
   const int ncopies = nbase + (sf.t_off ? 6 : 0) + (sf.src_off ? 1 : 0);
-  for (int c = lane; c < ncopies; c += 32) {
+  for (int c = first; c < ncopies; c += step) {
     if (c < 27) {
       const int ys = wrap(y - cy_of(c), Ny), zs = wrap(z - cz_of(c), Nz);
       bulk_copy_g2s(planes + (size_t)c * W, in.pops + (size_t)c * G.N + (size_t)(ys + Ny * zs) * W,
@@ -108,6 +121,17 @@ __device__ void issue_row(const Field<Elem>& in, const Grid& G, int W, int row, 
       bulk_copy_g2s(stage + sf.src_off, src + (size_t)row * W, W * sizeof(float), bar);
     }
   }
+}
+
+// All copies of one row, spread over the lanes of the calling warp (lane 0 posts the byte count
+// first).
+template <typename Elem>
+__device__ void issue_row(const Field<Elem>& in, const Grid& G, int W, int row, unsigned char* stage, uint64_t* bar,
+                          const StageFmt& sf, const typename Storage<Elem>::real* T6, const float* src) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) mbar_arrive_expect_tx(bar, sf.bytes);
+  __syncwarp();
+  issue_copies(in, G, W, row, stage, bar, sf, T6, src, lane, 32);
 }
 
 // Populations of node x from the staged row: plane i holds source row (y - c_iy, z - c_iz),
@@ -162,12 +186,13 @@ template <typename Elem, int WC>
 constexpr int rows_min_blocks() {
   return std::is_same<Elem, double>::value
              ? 1
-             : (block_threads(WC) == 384 ? 2 : (Storage<Elem>::dev && WC > 0 ? ELBM_ROWS_MINB_DEV : ELBM_ROWS_MINB));
+             : (block_threads(WC) == 384 ? (Storage<Elem>::dev ? ELBM_ROWS_MINB_384_DEV : ELBM_ROWS_MINB_384)
+                                          : (Storage<Elem>::dev && WC > 0 ? ELBM_ROWS_MINB_DEV : ELBM_ROWS_MINB));
 }
 
 }  // namespace
 
-// Next row for this block from the ticket counter (warp 0; the value is warp-uniform), or
+// Next row for this block from the ticket counter (one warp; the value is warp-uniform), or
 // nrows once the counter has run past the last row.
 __device__ __forceinline__ int take_row(unsigned long long* counters, int nrows, bool& exhausted) {
   int row = nrows;
@@ -191,107 +216,124 @@ __global__ void __launch_bounds__(block_threads(WC), rows_min_blocks<Elem, WC>()
 k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, Grid G,
             const typename Storage<Elem>::real* __restrict__ T6, const float* __restrict__ src,
             const float* __restrict__ u3, int fallback, unsigned long long* __restrict__ counters,
-            long long wait_limit, StageFmt sf, const PopConsts<typename Storage<Elem>::real> k) {
+            long long wait_limit, int withheld, StageFmt sf, const PopConsts<typename Storage<Elem>::real> k) {
   using R = typename Storage<Elem>::real;
+  constexpr int BT = block_threads(WC), NW = BT / 32;
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ uint64_t bars[STAGES];
-  __shared__ int s_row[STAGES];
-  __shared__ int abort_flag;
+  __shared__ uint64_t full[STAGES];           // completes when a stage's copies have landed
+  __shared__ int s_row[STAGES];               // row staged in each buffer (nrows: none)
+  __shared__ int s_next[2];                   // row of the refill of iteration it (parity it & 1)
   __shared__ float sE[Q];                     // E_i for the deviation decode (ordered by the first barrier)
   if (threadIdx.x < Q) sE[threadIdx.x] = float(k.E[threadIdx.x]);
   const int W = WC > 0 ? WC : G.nx;
   const size_t SB = sf.bytes;
   const int nrows = G.ny * G.nz;
-  const bool producer = threadIdx.x < 32;     // warp 0 takes the rows and issues their copies
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int b = 0; b < STAGES; ++b) mbar_init(&bars[b], 1);
+    for (int b = 0; b < STAGES; ++b) mbar_init(&full[b], 1 + withheld);   // withheld: test hook
     mbar_fence_init();
-    abort_flag = 0;
   }
   __syncthreads();
-  bool exhausted = false;
-  // thread 0: the ticket of the next row to issue, taken one iteration ahead so that the
-  // atomic's round trip overlaps a row of collisions instead of delaying warp 0
+  // thread 0: the ticket of the next row to issue, taken one row ahead so that the atomic's
+  // round trip overlaps a row of collisions
   unsigned long long pend = 0;
-  if (producer) {
-    for (int m = 0; m < STAGES - 1; ++m) {
+  if (warp == 0) {
+    bool exhausted = false;
+    for (int m = 0; m < STAGES; ++m) {
       const int row = take_row(counters, nrows, exhausted);
-      if (threadIdx.x == 0) s_row[m] = row;
-      if (row < nrows) issue_row(in, G, W, row, smem + m * SB, &bars[m], sf, T6, src);
+      if (lane == 0) s_row[m] = row;
+      if (row < nrows) issue_row(in, G, W, row, smem + m * SB, &full[m], sf, T6, src);
     }
-    if (!exhausted && threadIdx.x == 0) pend = atomicAdd(counters + TICKET, 1ull);
+    pend = exhausted ? (unsigned long long)nrows : 0ull;
+    if (!exhausted && lane == 0) pend = atomicAdd(counters + TICKET, 1ull);
   }
   __syncthreads();
   unsigned took = 0, proj = 0;
+  const int nper = (W + BT - 1) / BT;         // nodes of a row per thread (block-uniform)
+  // the copies of a refill are spread over all warps, so that no warp issues more than a few
+  // (one warp issues bulk copies at about one per 80 cycles)
+  const int cfirst = lane * NW + warp;
   int it = 0;
-  for (;; ++it) {
+  bool stop = false;
+  for (; !stop; ++it) {
     const int s = it % STAGES;
     const int row = s_row[s];
     if (row >= nrows) break;                  // rows are handed out in increasing order
-    if (producer) {
-      // the buffer of iteration it + STAGES - 1 was last read in iteration it - 1, which
-      // ended with a block barrier
-      const int sm = (it + STAGES - 1) % STAGES;
-      int nrow = nrows;
-      if (!exhausted) {
-        const unsigned long long t = __shfl_sync(0xffffffffu, pend, 0);
-        if (t < (unsigned long long)nrows) {
-          nrow = (int)t;
-          if (threadIdx.x == 0) pend = atomicAdd(counters + TICKET, 1ull);
-        } else {
-          exhausted = true;
-        }
+    const bool ok = mbar_wait_bounded(&full[s], (it / STAGES) & 1, wait_limit);
+    const unsigned char* stage = smem + s * SB;
+    const size_t row0 = (size_t)row * W;
+    for (int m = 0; m < nper; ++m) {
+      // threads past the end of the row read (and then drop) its last node, so that the pull is
+      // unconditional: a conditional pull makes the compiler spill the populations
+      const bool valid = ok && threadIdx.x + m * BT < W;
+      const int x = min(threadIdx.x + m * BT, W - 1);
+      const int n = (int)(row0 + x);
+      R g[Q];
+      staged_pull<Elem, R>(g, stage, W, x, sE);
+      Sym6<R> T;
+      if (sf.t_off) {
+        const R* Ts = reinterpret_cast<const R*>(stage + sf.t_off);
+        T = Sym6<R>{Ts[x], Ts[W + x], Ts[2 * W + x], Ts[3 * W + x], Ts[4 * W + x], Ts[5 * W + x]};
+      } else {
+        T = load_T<R>(T6, G.N, n, k.T);
       }
-      if (threadIdx.x == 0) s_row[sm] = nrow;
-      // ordering of the previous reads of this buffer before the copies: the block barrier
-      if (nrow < nrows) issue_row(in, G, W, nrow, smem + sm * SB, &bars[sm], sf, T6, src);
-    }
-    if (!mbar_wait_bounded(&bars[s], (it / STAGES) & 1, wait_limit)) {
-      abort_flag = 1;
-    } else {
-      const unsigned char* stage = smem + s * SB;
-      const size_t row0 = (size_t)row * W;
-      for (int x = threadIdx.x; x < W; x += block_threads(WC)) {
-        const int n = (int)(row0 + x);
-        R g[Q];
-        staged_pull<Elem, R>(g, stage, W, x, sE);
-        if (G.dirichlet) abb_faces<Elem, R>(g, in, G, x, n, k);
-        if (src != nullptr) {
-          // merged Strang half-steps of consecutive steps (Section 3.3)
-          const float sv = sf.src_off ? reinterpret_cast<const float*>(stage + sf.src_off)[x] : __ldg(src + n);
-          const R r = k.src_step * R(sv);
+      float sv = 0.f;
+      if (src != nullptr) sv = sf.src_off ? reinterpret_cast<const float*>(stage + sf.src_off)[x] : __ldg(src + n);
+      if (m == nper - 1) {
+        // every thread has read the stage of this row into registers: it is refilled with the
+        // row of iteration it + STAGES before the collisions, so that STAGES rows are in flight
+        // while this one is collided (the block barrier orders the generic reads of the buffer
+        // before the copies into it).  Thread 0 publishes the row and posts the byte count for
+        // the refill before the barrier (this phase of the buffer has completed: its wait
+        // succeeded); the same barrier tells every thread whether a wait of this row ran out,
+        // so that the whole block leaves together.
+        if (threadIdx.x == 0) {
+          const int nrow = pend < (unsigned long long)nrows ? (int)pend : nrows;
+          s_next[it & 1] = nrow;
+          if (ok && nrow < nrows) mbar_arrive_expect_tx(&full[s], sf.bytes);
+        }
+        if (__syncthreads_or(ok ? 0 : 1)) {
+          stop = true;
+          break;
+        }
+        const int nrow = s_next[it & 1];
+        if (threadIdx.x == 0) {
+          s_row[s] = nrow;
+          if (nrow < nrows) pend = atomicAdd(counters + TICKET, 1ull);
+        }
+        if (nrow < nrows) issue_copies(in, G, W, nrow, smem + s * SB, &full[s], sf, T6, src, cfirst, BT);
+      }
+      if (!valid) continue;
+      if (G.dirichlet) abb_faces<Elem, R>(g, in, G, x, n, k);
+      if (src != nullptr) {
+        // merged Strang half-steps of consecutive steps (Section 3.3)
+        const R r = k.src_step * R(sv);
 #pragma unroll
-          for (int i = 0; i < Q; ++i) g[i] += r * k.E[i];
-        }
-        Sym6<R> T;
-        if (sf.t_off) {
-          const R* Ts = reinterpret_cast<const R*>(stage + sf.t_off);
-          T = Sym6<R>{Ts[x], Ts[W + x], Ts[2 * W + x], Ts[3 * W + x], Ts[4 * W + x], Ts[5 * W + x]};
-        } else {
-          T = load_T<R>(T6, G.N, n, k.T);
-        }
-        R phi;
-        bool t;
-        if constexpr (VEL == 2) {
-          const R un[3] = {R(__ldg(u3 + n)), R(__ldg(u3 + G.N + n)), R(__ldg(u3 + 2 * G.N + n))};
-          t = collide_node<R, 2, ROOT>(g, T, k, fallback != 0, phi, un);
-        } else {
-          t = collide_node<R, VEL, ROOT>(g, T, k, fallback != 0, phi);
-        }
-        took += t ? 1u : 0u;
-        proj += Storage<Elem>::store(pout, sout, (int)G.N, n, g, k.Ek, phi, k.exact_mass != 0) ? 1u : 0u;
+        for (int i = 0; i < Q; ++i) g[i] += r * k.E[i];
       }
+      R phi;
+      bool t;
+      if constexpr (VEL == 2) {
+        const R un[3] = {R(__ldg(u3 + n)), R(__ldg(u3 + G.N + n)), R(__ldg(u3 + 2 * G.N + n))};
+        t = collide_node<R, 2, ROOT>(g, T, k, fallback != 0, phi, un);
+      } else {
+        t = collide_node<R, VEL, ROOT>(g, T, k, fallback != 0, phi);
+      }
+      took += t ? 1u : 0u;
+      proj += Storage<Elem>::store(pout, sout, (int)G.N, n, g, k.Ek, phi, k.exact_mass != 0) ? 1u : 0u;
     }
-    __syncthreads();
-    if (abort_flag) break;
   }
-  if (abort_flag && threadIdx.x == 0) {
+  if (stop) --it;                             // the aborted iteration
+  if (stop && threadIdx.x == 0) {
     // leave no copy in flight into this block's shared memory (waits bounded): the buffers
     // hold the rows of iterations it .. it + STAGES - 1, issued where s_row < nrows
     atomicExch(counters + 2, 1ull);
     for (int m = it; m < it + STAGES; ++m)
-      if (s_row[m % STAGES] < nrows) mbar_wait_bounded(&bars[m % STAGES], (m / STAGES) & 1, WAIT_LIMIT);
+      if (s_row[m % STAGES] < nrows) {
+        for (int w = 0; w < withheld; ++w) mbar_arrive(&full[m % STAGES]);   // the arrivals the test withheld
+        mbar_wait_bounded(&full[m % STAGES], (m / STAGES) & 1, WAIT_LIMIT);
+      }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) took += __shfl_xor_sync(0xffffffffu, took, o);
@@ -555,7 +597,7 @@ cudaError_t launch_rows_t(const StepLaunch& L, cudaStream_t s) {
   using R = typename Storage<Elem>::real;
   // stage the T-field and source rows too where that keeps the resident blocks per SM
   const StageFmt base = stage_fmt<Elem>(L.nx, false, false, 0);
-  StageFmt sf = stage_fmt<Elem>(L.nx, L.T6 != nullptr, L.src != nullptr, 200 * 1024);
+  StageFmt sf = stage_fmt<Elem>(L.nx, L.T6 != nullptr, L.src != nullptr, ELBM_ROWS_FIELD_BUDGET);
   int nb = rows_occupancy<Elem, VEL, ROOT, WC>(STAGES * (size_t)base.bytes);
   if (sf.bytes != base.bytes) {
     const int nbf = rows_occupancy<Elem, VEL, ROOT, WC>(STAGES * (size_t)sf.bytes);
@@ -586,7 +628,7 @@ cudaError_t launch_rows_t(const StepLaunch& L, cudaStream_t s) {
                                                                                                : (const void*)L.kf);
   k_step_rows<Elem, VEL, ROOT, WC><<<grid, block_threads(WC), STAGES * (size_t)sf.bytes, s>>>(
       in, static_cast<Elem*>(L.pout), L.sout, G, static_cast<const R*>(L.T6), L.src, L.u3, L.fallback, L.counters,
-      L.wait_limit > 0 ? L.wait_limit : WAIT_LIMIT, sf, k);
+      L.wait_limit > 0 ? L.wait_limit : WAIT_LIMIT, L.withheld, sf, k);
   return cudaGetLastError();
 }
 

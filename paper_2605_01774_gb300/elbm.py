@@ -67,6 +67,7 @@ def lib() -> C.CDLL:
         "elbm_set_lambda_mode": (S, [H, C.c_int32]),
         "elbm_set_step_kernel": (S, [H, C.c_int32]),
         "elbm_set_wait_limit": (S, [H, I64]),
+        "elbm_set_wait_test": (S, [H, C.c_int32]),
         "elbm_get_step_kernel": (S, [H, C.POINTER(C.c_int32)]),
         "elbm_set_exact_mass": (S, [H, C.c_int32]),
         "elbm_storage_projections": (S, [H, C.POINTER(C.c_int64)]),
@@ -239,6 +240,10 @@ def elbm_set_step_kernel(h, variant):
 
 def elbm_set_wait_limit(h, cycles):
     _check(lib().elbm_set_wait_limit(h, int(cycles)), h)
+
+
+def elbm_set_wait_test(h, withheld):
+    _check(lib().elbm_set_wait_test(h, int(withheld)), h)
 
 
 def elbm_set_exact_mass(h, on):

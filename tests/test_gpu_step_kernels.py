@@ -184,11 +184,13 @@ def test_automatic_choice(E):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16dev"])
-@pytest.mark.parametrize("variant", [3])
+@pytest.mark.parametrize("variant", [2, 3])
 def test_staging_wait_limit_timeout_and_recovery(E, prec, variant):
-    """A staging wait limit far below a copy's latency makes the pipelined kernel give up:
-    blocks raise their abort flag, the producer waits (with the full limit) for the copies it
-    issued, and the next synchronise reports ELBM_ERR_TIMEOUT.  With the limit restored the same
+    """A staging wait limit far below a copy's latency makes the staged-row kernels give up:
+    blocks raise their abort flag, the thread that issued the copies waits (with the full limit)
+    for those still in flight, and the next synchronise reports ELBM_ERR_TIMEOUT.  Variant 2 is
+    made to time out by stage barriers that expect one arrival too many (elbm_set_wait_test);
+    its abort path makes that arrival before it waits for the copies.  With the limit restored the same
     handle steps normally again and matches a fresh handle bit for bit."""
     dims = (256, 16, 12)
     D6, phi0, src = _case(dims, 9)
@@ -196,12 +198,19 @@ def test_staging_wait_limit_timeout_and_recovery(E, prec, variant):
     lat = gpu_lattice(E, dims, prec, D6_field=D6, u=u, source=src)
     E.elbm_set_step_kernel(lat.h, variant)
     E.elbm_init_equilibrium(lat.h, torch.as_tensor(phi0, device="cuda"))
-    E.elbm_set_wait_limit(lat.h, 16)
+    if variant == 2:
+        # the staged-row kernel issues its first rows before any wait, so a short limit alone
+        # may find them landed: its barriers are made to expect one arrival that never comes
+        E.elbm_set_wait_test(lat.h, 1)
+        E.elbm_set_wait_limit(lat.h, 4096)
+    else:
+        E.elbm_set_wait_limit(lat.h, 16)
     E.elbm_step(lat.h, 1)
     with pytest.raises(E.ElbmError) as ei:
         E.elbm_synchronize(lat.h)
     assert ei.value.status == 7
     E.elbm_set_wait_limit(lat.h, 0)
+    E.elbm_set_wait_test(lat.h, 0)
     E.elbm_synchronize(lat.h)                             # the flag was cleared
     E.elbm_init_equilibrium(lat.h, torch.as_tensor(phi0, device="cuda"))
     E.elbm_step(lat.h, 4)
