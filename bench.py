@@ -171,7 +171,7 @@ def run_ours(args, rank, world, local, dist):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     E.lib()
-    wl = synth.gaussian_plume(n=args.size)
+    wl = synth.gaussian_plume(n=args.size, dims=args.dims if args.only else None)
     D6 = synth.d6_from_matrix(wl.D)
     N = int(np.prod(wl.dims))
     stream = torch.cuda.Stream(device=dev)
@@ -214,7 +214,7 @@ def run_ours(args, rank, world, local, dist):
     if args.only and args.workload == "heterogeneous":
         # the 384^3 two-phase porous workload (per-node tensor field, Gaussian source, Dirichlet
         # x faces, u = 0): a parity-test configuration, timed here for one form
-        hw = synth.heterogeneous(n=args.size if args.size != 256 else 384)
+        hw = synth.heterogeneous(n=args.size if args.size != 256 else 384, dims=args.dims)
         Nh = int(np.prod(hw.dims))
         lat = E.Lattice(hw.dims, args.only, bc=hw.dirichlet_x, stream=stream)
         E.elbm_set_tensor_field(lat.h, torch.as_tensor(hw.D6_field, dtype=torch.float32, device=dev))
@@ -708,6 +708,8 @@ def main():
     ap.add_argument("--form", default="f32", choices=["f16dev", "bf16dev", "f32"],
                     help="headline (chosen) form")
     ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--dims", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
+                    help="with --only: a box of this shape instead of the cube (smaller profiling cases)")
     ap.add_argument("--err-steps", type=int, default=200)
     ap.add_argument("--cpu-sample", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
