@@ -79,27 +79,43 @@ def ncu_traffic(form: str):
 
 
 class ClockSampler:
-    """nvidia-smi SM clocks and throttle reasons sampled every 200 ms during the timed region."""
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    """nvidia-smi SM clocks and throttle reasons sampled every 10 ms, started a moment before the
+    timed region; the summary keeps the samples whose timestamps fall inside the region (host
+    clock from just before the first timed launch to just after the last one completed), so that
+    a timed region of a few milliseconds still has its own samples and idle samples around it do
+    not count."""
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
+    LEAD_S = 0.3   # nvidia-smi's start-up before the first sample
 
     def __init__(self, device: int):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.device = device
         self.p = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200", "-i", str(self.device)], stdout=self.f,
+                                       "-lms", "10", "-i", str(self.device)], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
+            time.sleep(self.LEAD_S)
         except (OSError, FileNotFoundError):
             self.p = None
         return self
 
+    def start(self):
+        """Mark the start of the timed region (call just before its first launch)."""
+        self.t0 = time.time()
+
+    def stop(self):
+        """Mark its end (call once its last launch has completed)."""
+        self.t1 = time.time()
+
     def __exit__(self, *a):
         if self.p is not None:
+            time.sleep(0.03)   # let the sample that follows the region land
             self.p.terminate()
             try:
                 self.p.wait(timeout=5)
@@ -107,23 +123,37 @@ class ClockSampler:
                 self.p.kill()
 
     def summary(self):
+        import datetime
         self.f.flush()
         rows = []
         for line in open(self.f.name):
             parts = [s.strip() for s in line.split(",")]
-            if len(parts) < 7:
+            if len(parts) < 8:
                 continue
             try:
-                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[1]), float(parts[2]), parts[4:8]))
             except ValueError:
                 continue
         os.unlink(self.f.name)
-        if not rows:
+        inside = [r for r in rows if self.t0 is not None and self.t1 is not None and self.t0 <= r[0] <= self.t1]
+        note = None
+        if not inside and rows and self.t0 is not None and self.t1 is not None:
+            # a region shorter than the sampling interval: the sample nearest to it, marked as such
+            near = min(rows, key=lambda r: max(self.t0 - r[0], r[0] - self.t1, 0.0))
+            note = f"no sample inside the {1e3 * (self.t1 - self.t0):.1f} ms region; nearest " \
+                   f"{1e3 * max(self.t0 - near[0], near[0] - self.t1, 0.0):.1f} ms from it"
+            inside = [near]
+        if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[2][k].lower().startswith("active")})
-        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+        reasons = sorted({names[k] for r in inside for k in range(4) if r[3][k].lower().startswith("active")})
+        out = {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+               "reasons": reasons, "samples": len(inside) if note is None else 0,
+               "interval_ms": 10, "region_ms": round(1e3 * (self.t1 - self.t0), 2)}
+        if note:
+            out["note"] = note
+        return out
 
 
 def dist_setup(n_gpus: int):
@@ -196,11 +226,13 @@ def run_ours(args, rank, world, local, dist):
         sampler = ClockSampler(local) if sample_clocks else None
         if sampler:
             sampler.__enter__()
+            sampler.start()
         ev0.record(stream)
         E.elbm_step(lat.h, K)
         ev1.record(stream)
         ev1.synchronize()
         if sampler:
+            sampler.stop()
             sampler.__exit__(None, None, None)
         torch.cuda.synchronize(dev)
         barrier(dist)
@@ -384,10 +416,12 @@ def late_window(args, E, lat, stream, dev, dist, N, fb_so_far, local):
     sampler = ClockSampler(local)
     sampler.__enter__()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.start()
     ev0.record(stream)
     E.elbm_step(lat.h, args.late_window)
     ev1.record(stream)
     ev1.synchronize()
+    sampler.stop()
     sampler.__exit__(None, None, None)
     ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev) / args.late_window
     fb1 = E.elbm_reduce(lat.h, allow_nonfinite=True)["n_fallback"]

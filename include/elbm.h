@@ -359,6 +359,19 @@ elbm_status elbm_relaxation_complement(const double D6[6], double T6_out[6]);
  * ELBM_ERR_CUDA on a runtime error.  Takes a few milliseconds; synchronises. */
 elbm_status elbm_fma_peak(int32_t precision, double* flops_per_s);
 
+/* Measured rate of bulk asynchronous global -> shared copies (cp.async.bulk completing on an
+ * mbarrier) on the current device: blocks_per_sm persistent 256-thread blocks per SM, in each
+ * of which warp 0 issues the copies (copy_bytes each, 24 KiB per stage, two stages) of a 1 GiB
+ * source.  Returns the bytes and the copies per second of the whole device, best of three
+ * timed launches.  It shows how fast one warp issues such copies (with small copies and few
+ * issuing warps the issue rate, not DRAM, bounds the bytes), which is why the staged-row step
+ * spreads a row's copies over all warps.  The paper has no counterpart.  ELBM_ERR_ARG unless
+ * copy_bytes is a multiple of 16 in [16, 24576] and 1 <= blocks_per_sm <= 4, ELBM_ERR_OOM if
+ * the 1 GiB source cannot be allocated, ELBM_ERR_TIMEOUT if a copy wait ran out (about one
+ * second), ELBM_ERR_CUDA on a runtime error.  Allocates and frees device memory; synchronises. */
+elbm_status elbm_bulk_copy_rate(int32_t copy_bytes, int32_t blocks_per_sm, double* bytes_per_s,
+                                double* copies_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -89,6 +89,7 @@ def lib() -> C.CDLL:
         "elbm_check_velocity": (S, [D]),
         "elbm_relaxation_complement": (S, [D, D]),
         "elbm_fma_peak": (S, [C.c_int32, C.POINTER(C.c_double)]),
+        "elbm_bulk_copy_rate": (S, [C.c_int32, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     }
     I32, PI32, PI64 = C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64)
     sig.update({
@@ -526,6 +527,13 @@ def elbm_fma_peak(prec="f64") -> float:
     v = C.c_double(0.0)
     _check(lib().elbm_fma_peak(PRECISIONS[prec], C.byref(v)))
     return float(v.value)
+
+
+def elbm_bulk_copy_rate(copy_bytes, blocks_per_sm=2):
+    """(bytes/s, copies/s) of bulk asynchronous global -> shared copies issued by one warp per block."""
+    b, c = C.c_double(0), C.c_double(0)
+    _check(lib().elbm_bulk_copy_rate(int(copy_bytes), int(blocks_per_sm), C.byref(b), C.byref(c)))
+    return b.value, c.value
 
 
 # ------------------------------------------------------------------- D2Q9 (include/elbm2d.h)

@@ -41,6 +41,14 @@ def test_host_only_validation():
     assert np.allclose(T[[0, 3, 5]], 12 * d / (1 + 6 * d), rtol=1e-15)
 
 
+def test_bulk_copy_rate_rejects_bad_arguments():
+    from paper_2605_01774_gb300 import elbm as E
+    for size, bps in ((8, 1), (24, 1), (32768, 1), (512, 0), (512, 5)):
+        with pytest.raises(E.ElbmError) as ei:
+            E.elbm_bulk_copy_rate(size, bps)
+        assert ei.value.status == 1
+
+
 def test_host_only_validation_2d():
     import numpy as np
     from paper_2605_01774_gb300 import elbm as E
