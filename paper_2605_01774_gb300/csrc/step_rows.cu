@@ -123,6 +123,60 @@ __device__ void issue_copies(const Field<Elem>& in, const Grid& G, int W, int ro
   }
 }
 
+// One copy of a row's refill, fixed for the launch: the source plane's first row, the copy's
+// offset in the stage, and the row bytes with the (cy, cz) shift of the source row packed in
+// `meta` (bits 0-15 bytes, 16-19 cy + 1, 20-23 cz + 1).  Copy c of row (y, z) reads the plane's
+// row (y - cy, z - cz), wrapped, as issue_copies does.
+struct __align__(16) CopyDesc {
+  const unsigned char* plane;
+  unsigned dst;
+  unsigned meta;
+};
+
+template <typename Elem>
+__device__ CopyDesc copy_desc(const Field<Elem>& in, const Grid& G, int W, const StageFmt& sf,
+                              const typename Storage<Elem>::real* T6, const float* src, int c) {
+  using R = typename Storage<Elem>::real;
+  constexpr bool dev = Storage<Elem>::dev;
+  constexpr int nbase = dev ? 36 : 27;
+  const unsigned char* plane;
+  unsigned dst, bytes;
+  int cy = 0, cz = 0;
+  if (c < 27) {
+    plane = reinterpret_cast<const unsigned char*>(in.pops + (size_t)c * G.N);
+    dst = (unsigned)((size_t)c * W * sizeof(Elem));
+    bytes = W * sizeof(Elem);
+    cy = cy_of(c);
+    cz = cz_of(c);
+  } else if (dev && c < nbase) {
+    const int r = c - 27;                              // scale row r = 3 (cy + 1) + (cz + 1)
+    plane = reinterpret_cast<const unsigned char*>(in.scale);
+    dst = (unsigned)(27ull * W * sizeof(Elem) + (size_t)r * W * sizeof(float));
+    bytes = W * sizeof(float);
+    cy = r / 3 - 1;
+    cz = r % 3 - 1;
+  } else if (sf.t_off && c < nbase + 6) {
+    const int q = c - nbase;                           // T component q of the destination row
+    plane = reinterpret_cast<const unsigned char*>(T6 + (size_t)q * G.N);
+    dst = sf.t_off + (unsigned)((size_t)q * W * sizeof(R));
+    bytes = W * sizeof(R);
+  } else {
+    plane = reinterpret_cast<const unsigned char*>(src);
+    dst = sf.src_off;
+    bytes = W * sizeof(float);
+  }
+  return CopyDesc{plane, dst, bytes | (unsigned)(cy + 1) << 16 | (unsigned)(cz + 1) << 20};
+}
+
+// The copy of descriptor d for the row (y, z) (one bulk copy of d's row bytes).
+__device__ __forceinline__ void issue_desc(const CopyDesc& d, int y, int z, const Grid& G, unsigned char* stage,
+                                           uint64_t* bar) {
+  const unsigned bytes = d.meta & 0xffffu;
+  const int ys = wrap(y - (int)((d.meta >> 16) & 15u) + 1, G.ny);
+  const int zs = wrap(z - (int)((d.meta >> 20) & 15u) + 1, G.nz);
+  bulk_copy_g2s(stage + d.dst, d.plane + (size_t)(ys + G.ny * zs) * bytes, bytes, bar);
+}
+
 // All copies of one row, spread over the lanes of the calling warp (lane 0 posts the byte count
 // first).
 template <typename Elem>
@@ -223,9 +277,13 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
   __shared__ uint64_t full[STAGES];           // completes when a stage's copies have landed
   __shared__ int s_row[STAGES];               // row staged in each buffer (nrows: none)
   __shared__ int s_next[2];                   // row of the refill of iteration it (parity it & 1)
+  __shared__ int2 s_nyz[2];                   // its (y, z)
   __shared__ float sE[Q];                     // E_i for the deviation decode (ordered by the first barrier)
+  __shared__ CopyDesc s_desc[48];             // the refill's copies (ordered by the first barrier)
   if (threadIdx.x < Q) sE[threadIdx.x] = float(k.E[threadIdx.x]);
   const int W = WC > 0 ? WC : G.nx;
+  const int ncopies = (Storage<Elem>::dev ? 36 : 27) + (sf.t_off ? 6 : 0) + (sf.src_off ? 1 : 0);
+  if (threadIdx.x < ncopies) s_desc[threadIdx.x] = copy_desc(in, G, W, sf, T6, src, threadIdx.x);
   const size_t SB = sf.bytes;
   const int nrows = G.ny * G.nz;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -291,6 +349,7 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
         if (threadIdx.x == 0) {
           const int nrow = pend < (unsigned long long)nrows ? (int)pend : nrows;
           s_next[it & 1] = nrow;
+          s_nyz[it & 1] = make_int2(nrow % G.ny, nrow / G.ny);
           if (ok && nrow < nrows) mbar_arrive_expect_tx(&full[s], sf.bytes);
         }
         if (__syncthreads_or(ok ? 0 : 1)) {
@@ -302,7 +361,12 @@ k_step_rows(Field<Elem> in, Elem* __restrict__ pout, float* __restrict__ sout, G
           s_row[s] = nrow;
           if (nrow < nrows) pend = atomicAdd(counters + TICKET, 1ull);
         }
-        if (nrow < nrows) issue_copies(in, G, W, nrow, smem + s * SB, &full[s], sf, T6, src, cfirst, BT);
+        // this thread's copy of the refill (the same copy in every row, one per thread at most:
+        // ncopies <= 43 < BT), from its launch-long descriptor
+        if (nrow < nrows && cfirst < ncopies) {
+          const int2 yz = s_nyz[it & 1];
+          issue_desc(s_desc[cfirst], yz.x, yz.y, G, smem + s * SB, &full[s]);
+        }
       }
       if (!valid) continue;
       if (G.dirichlet) abb_faces<Elem, R>(g, in, G, x, n, k);
