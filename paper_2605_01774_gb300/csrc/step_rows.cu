@@ -4,16 +4,18 @@
 // each row it stages in shared memory, with cp.async.bulk copies completing on an
 // mbarrier, the 27 whole source rows the pull needs -- population plane i, row
 // (y - c_iy, z - c_iz) -- and, for the deviation storages, the 9 rows of the FP32 scale
-// plane.  The periodic x-shift is an index wrap inside the staged row.  STAGES buffers
-// rotate without a block barrier: each warp counts itself on a stage once it has read its
-// nodes' populations into registers, and the last warp to do so refills that stage with the
-// next row (the row index is published with the stage's mbarrier), so the copies of the next
-// STAGES rows are in flight while the current one is collided, a warp that meets costly nodes
-// (positivity fallback, boundary faces) delays only the refill of the stage it is reading,
-// and memory parallelism does not depend on registers.  Rows are handed out dynamically so
-// that blocks meeting costly rows do not set the kernel's length.  Collision and store are
-// those of the one-thread-per-node kernel, in the same order, so both give bit-equal results.
-// Requires Nx % 8 == 0 (16-byte aligned rows); every wait is bounded.
+// plane (with a per-node tensor field or source, also the destination row's T and source
+// rows).  The periodic x-shift is an index wrap inside the staged row.  STAGES buffers
+// rotate: once every thread has read its nodes' populations of a row into registers (one
+// block barrier), the buffer is refilled with the row STAGES ahead before the collisions,
+// its copies spread over all warps (one warp issues bulk copies at about one per 80
+// cycles), so the next rows' copies are in flight while this one is collided and memory
+// parallelism does not depend on registers.  Rows are handed out dynamically so that
+// blocks meeting costly rows (positivity fallback, boundary faces) do not set the
+// kernel's length.  Collision and store are those of the one-thread-per-node kernel, in
+// the same order, so both give bit-equal results.  A second kernel in this file
+// (k_step_pipe) replaces the block barrier by a producer warp and full/empty mbarriers
+// per stage.  Requires Nx % 8 == 0 (16-byte aligned rows); every wait is bounded.
 #include <algorithm>
 
 #include "bulk.cuh"
